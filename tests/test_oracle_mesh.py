@@ -1,0 +1,168 @@
+"""Pins of the oracle's spacetree: balance, face coverage, skeleton, remesh."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import ader, basis, mesh as meshmod
+from oracle_helpers import refined_mesh
+
+
+def boxes(m):
+    out = []
+    for k in m.cells:
+        h = m.width(k[0])
+        a = m.lo + np.asarray(k[1], dtype=np.float64) * h
+        out.append((a, a + h))
+    return out
+
+
+def touching_levels_bruteforce(m):
+    """For every cell, the levels of all leaves that share a (d-1)-dimensional
+    piece of face with it, found by box geometry with periodic shifts
+    (vectorised over the other cells)."""
+    bx = boxes(m)
+    A = np.array([a for a, _ in bx])
+    Bb = np.array([b for _, b in bx])
+    lv = np.array([k[0] for k in m.cells])
+    L = m.hi - m.lo
+    res = []
+    tol = 1e-12
+    for i in range(len(bx)):
+        a, b = A[i], Bb[i]
+        found = set()
+        for shift in itertools.product((-1, 0, 1), repeat=m.dim):
+            sh = np.asarray(shift) * L
+            c2, d2 = A + sh, Bb + sh
+            touch = (np.abs(b - c2) < tol) | (np.abs(d2 - a) < tol)
+            overlap = (np.minimum(b, d2) - np.maximum(a, c2)) > tol
+            ok = (touch.sum(axis=1) == 1) & ((overlap & ~touch).sum(axis=1) == m.dim - 1)
+            found.update(lv[ok].tolist())
+        res.append(found)
+    return res
+
+
+@pytest.mark.parametrize("dim,base", [(2, 3), (2, 9), (3, 3)])
+def test_uniform_faces(dim, base):
+    m = meshmod.Mesh(dim, (base,) * dim, 2)
+    conf, parents = m.faces()
+    assert len(conf) == dim * base ** dim and not parents
+    assert not m.skeleton().any()
+
+
+@pytest.mark.parametrize("dim,base,levels", [(2, 9, 2), (2, 3, 2), (3, 3, 1), (3, 3, 2)])
+def test_refined_mesh_balance_coverage_skeleton(dim, base, levels):
+    m = refined_mesh(dim, base, levels, (0.45,) * dim, 0.2)
+    lv = np.array([k[0] for k in m.cells])
+    assert lv.max() == levels and lv.min() == 0
+    # leaves tile the domain
+    vol = np.prod(m.cell_widths(), axis=1).sum()
+    assert abs(vol - 1.0) < 1e-12
+    # 2:1 balance by geometry, and the skeleton = cells touching another level
+    touch = touching_levels_bruteforce(m)
+    skel_geo = np.zeros(len(m.cells), dtype=bool)
+    for i, k in enumerate(m.cells):
+        assert all(abs(l - k[0]) <= 1 for l in touch[i])
+        skel_geo[i] = any(l != k[0] for l in touch[i])
+    assert np.array_equal(skel_geo, m.skeleton())
+    # every face slot of every cell is covered exactly once
+    conf, parents = m.faces()
+    count = np.zeros((len(m.cells), dim, 2), dtype=int)
+    for a, b, dr in conf:
+        count[a, dr, 1] += 1
+        count[b, dr, 0] += 1
+    for c, dr, side, kids in parents:
+        count[c, dr, side] += 1
+        assert len(kids) == 3 ** (dim - 1)
+        for f, _ in kids:
+            count[f, dr, 1 - side] += 1
+            assert m.cells[f][0] == m.cells[c][0] + 1
+    assert np.all(count == 1)
+
+
+def test_balance_cascade():
+    """Refining a corner cell twice forces the neighbours of the level-2
+    cells to level >= 1 (a balance cascade), never more."""
+    m = meshmod.Mesh(2, (3, 3), 3)
+    B = basis.Basis(1)
+    u = np.zeros((9, 1, 2, 2))
+    flags = np.zeros(9, dtype=np.int8)
+    flags[m.index[(0, (1, 1))]] = 1
+    u = m.remesh(u, flags, B)
+    flags = np.array([1 if k == (1, (3, 3)) else 0 for k in m.cells], dtype=np.int8)
+    u = m.remesh(u, flags, B)
+    lv = {k: k[0] for k in m.cells}
+    assert max(lv.values()) == 2
+    for i, ls in enumerate(touching_levels_bruteforce(m)):
+        assert all(abs(l - m.cells[i][0]) <= 1 for l in ls)
+    # the level-2 cells sit in (1,(3,3)); its face neighbours at level 1 exist
+    assert (1, (2, 3)) in m.leaves and (1, (3, 2)) in m.leaves
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_remesh_transfer_identities(dim):
+    """Refine then coarsen is the identity on the polynomial data; both keep
+    the integral of every variable (conservative transfer)."""
+    N = 3
+    B = basis.Basis(N)
+    m = meshmod.Mesh(dim, (3,) * dim, 1)
+    rng = np.random.default_rng(4)
+    u0 = rng.standard_normal((len(m.cells), 2) + (B.n,) * dim)
+    I0 = ader.cell_integral(u0, m.cell_widths(), B)
+    flags = np.zeros(len(m.cells), dtype=np.int8)
+    flags[[0, 4]] = 1
+    u1 = m.remesh(u0, flags, B)
+    assert len(m.cells) == 3 ** dim - 2 + 2 * 3 ** dim
+    assert np.allclose(ader.cell_integral(u1, m.cell_widths(), B), I0, atol=1e-13)
+    flags = np.array([-1 if k[0] == 1 else 0 for k in m.cells], dtype=np.int8)
+    u2 = m.remesh(u1, flags, B)
+    assert len(m.cells) == 3 ** dim
+    assert np.allclose(u2, u0, atol=1e-13)
+    # coarsening of non-polynomial children: L2 projection keeps integrals
+    m.remesh(u2, np.array([1 if i == 2 else 0 for i in range(len(m.cells))]), B)
+    u3 = rng.standard_normal((len(m.cells), 2) + (B.n,) * dim)
+    I3 = ader.cell_integral(u3, m.cell_widths(), B)
+    flags = np.array([-1 if k[0] == 1 else 0 for k in m.cells], dtype=np.int8)
+    u4 = m.remesh(u3, flags, B)
+    assert np.allclose(ader.cell_integral(u4, m.cell_widths(), B), I3, atol=1e-13)
+
+
+def test_coarsen_blocked_by_balance():
+    """A family may not coarsen while a leaf two levels finer than the parent
+    touches the parent's faces."""
+    m = meshmod.Mesh(2, (3, 3), 3)
+    B = basis.Basis(1)
+    u = np.zeros((9, 1, 2, 2))
+    u = m.remesh(u, [1 if k == (0, (1, 1)) else 0 for k in m.cells], B)
+    u = m.remesh(u, [1 if k == (1, (3, 4)) else 0 for k in m.cells], B)   # left child column
+    # ask every level-1 cell in parent (0,(1,1)) to coarsen: blocked? the
+    # level-2 cells are inside that family, so (1,(3,4)) is not a leaf -> no
+    fl = [-1 if k[0] == 1 and k[1][0] // 3 == 1 and k[1][1] // 3 == 1 else 0 for k in m.cells]
+    n_before = len(m.cells)
+    u = m.remesh(u, fl, B)
+    assert len(m.cells) == n_before
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_prolong_face_equals_extrapolated_prolong_volume(dim):
+    """Face-only prolongation (virtual-cell faces) equals extrapolating the
+    volume interpolation of the coarse cell into the virtual cell."""
+    N = 4
+    B = basis.Basis(N)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 3) + (B.n,) * dim)
+    for dr in range(dim):
+        for side in range(2):
+            face = ader.face_values(x, dr, side, B)
+            for s in meshmod.subface_indices(dim, dr):
+                full = []
+                t = 0
+                for a in range(dim):
+                    if a == dr:
+                        full.append(0 if side == 0 else 2)
+                    else:
+                        full.append(s[t])
+                        t += 1
+                vol = ader.prolong_volume(x, tuple(full), B)
+                ref = ader.face_values(vol, dr, side, B)
+                assert np.allclose(ader.prolong_face(face, s, B, dim), ref, atol=1e-13)
