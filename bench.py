@@ -1,0 +1,394 @@
+"""Throughput of the adaptive 3D Euler ADER-DG step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload euler3d-n5-amr | euler3d-n7-amr | euler2d-n3-vortex]
+                    [--precision fp64|fp32]
+
+Default workload: 3D compressible Euler, order N = 5 (6^3 Gauss-Legendre nodes
+per cell, 5 variables), spacetree base 27^3 on the periodic unit cube, 3:1
+refinement to 2 extra levels inside a ball of radius 0.15 around a Gaussian
+density bubble (amplitude 0.2 on rho = 1, p = 1, v = (1, 1, 1)), 2:1 balanced,
+remeshing every 10 steps as the ball moves with the flow, skeleton/enclave
+streams, FP64.  One bench step = one full ADER-DG time step (predictor,
+prolongation, Riemann, restriction, corrector, CFL reduction; the remesh of
+every 10th step is inside the timed region).
+
+Metric: DoF-updates/s = sum over cells of m n^3, times steps, over time.
+Multi-GPU runs (torchrun) are independent replicas, one per rank (weak
+scaling); the value sums all ranks' DoF-updates over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "3D Euler ADER-DG DoF-updates/s on 1 GB300; mixed vs FP64 at same L2 err"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (nominal); a pure DFMA loop measured 1.20
+FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 128 FP32 lanes/SM, FMA = 2 flops
+
+WORKLOADS = {
+    "euler3d-n5-amr": dict(dim=3, order=5, base=27, max_level=2, radius=0.15, remesh_every=10,
+                           init="bubble"),
+    "euler3d-n7-amr": dict(dim=3, order=7, base=27, max_level=2, radius=0.15, remesh_every=10,
+                           init="bubble"),
+    "euler2d-n3-vortex": dict(dim=2, order=3, base=27, max_level=0, radius=0.0, remesh_every=0,
+                              init="vortex"),
+}
+
+
+def predictor_flops_per_cell(dim, order, iters, m):
+    """Algorithmic flops of the fused predictor per cell (FMA = 2).
+
+    c_f = 29 flops per Euler flux evaluation (all dim directions, 3D) scaled
+    by dimension; first Picard iteration needs one time slice (constant
+    initial guess); each later iteration n slices of flux, divergence
+    (dim m dot products of length n plus scaling) and time mixing (n m FMAs);
+    then time averages, the volume term and face extrapolation."""
+    n = order + 1
+    NS = n ** dim
+    NF = n ** (dim - 1)
+    c_f = 1 + dim + 2 * dim + 3 + 1 + dim * (dim + 2)
+    slice_cost = c_f + dim * m * (2 * n + 2) + 2 * n * m
+    per_node = slice_cost + (iters - 1) * n * slice_cost
+    per_node += n * (c_f + 2 * m * (1 + dim)) + dim * m * (2 * n + 2)
+    return NS * per_node + 2 * dim * NF * 2 * m * 2 * n
+
+
+def predictor_bytes_per_cell(dim, order, m):
+    """Algorithmic HBM bytes of the fused predictor per cell: read u, write u*
+    and the 2d face blocks (Q-bar and F-bar)."""
+    n = order + 1
+    return 8 * (2 * m * n ** dim + 2 * 2 * dim * m * n ** (dim - 1))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), reasons=parts[4:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for nm, v in zip(names[1:], r["reasons"][1:]):
+                if v.lower() in ("active", "1", "yes"):
+                    seen.add(nm)
+        return {"sm_mhz": float(np.median([r["sm"] for r in rows])),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(seen),
+                "samples": len(rows)}
+
+
+def build_problem(wl, precision, device):
+    from paper_1806_07984_gb300 import Solver
+    dim, order = wl["dim"], wl["order"]
+    s = Solver(dim, order, "euler", base=(wl["base"],) * 3, max_level=wl["max_level"],
+               cfl=workloads.ADER_CFL[order], precision=precision, device=device)
+    center = workloads.sphere_center(0.0)[:dim]
+    for _ in range(wl["max_level"]):
+        s.remesh(s.sphere_flags(center, wl["radius"]))
+    if wl["max_level"] > 0:
+        s.classify(s.sphere_flags(center, wl["radius"]))
+    X = s.node_coords()
+    if wl["init"] == "bubble":
+        u = workloads.density_bubble(X)
+    else:
+        u = workloads.isentropic_vortex(X[0], X[1])
+    u = np.ascontiguousarray(np.moveaxis(u, 0, 1))
+    return s, u
+
+
+def dofs_of(s):
+    return s.ncells * s.nvar * s.n ** s.dim
+
+
+def run_steps(s, wl, k, t_dev, step_base):
+    """k full steps; every remesh_every-th step is followed by a remesh at the
+    ball's current position and a reclassification of the skeleton."""
+    dofs = 0
+    for i in range(k):
+        dofs += dofs_of(s)
+        s.step(1)
+        t_dev.add_(s.dt)
+        j = step_base + i + 1
+        if wl["remesh_every"] and j % wl["remesh_every"] == 0:
+            t = float(t_dev.item())
+            center = workloads.sphere_center(t)[:wl["dim"]]
+            s.remesh(s.sphere_flags(center, wl["radius"]))
+            s.classify(s.sphere_flags(center, wl["radius"]))
+    return dofs
+
+
+def time_predictor(s, torch, reps=3):
+    """Average duration of one ader_predict(ADER_ALL) launch, CUDA events on
+    the launching stream."""
+    from paper_1806_07984_gb300 import ader as A
+    st = torch.cuda.current_stream()
+    s.predict(A.ADER_ALL, stream=st)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        s.predict(A.ADER_ALL, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def cpu_baseline(wl_name, wl, seconds=15.0):
+    """Oracle (numpy FP64, one BLAS thread) on a bounded sample: full oracle
+    steps on the same PDE/order/refinement rule on a base 3^3 mesh."""
+    code = r"""
+import os, sys, time, json
+import numpy as np
+sys.path.insert(0, %r)
+from oracle import ader, basis, mesh as omesh, pde as opde, step as ostep
+import workloads
+dim, order, lvl, radius, budget = %d, %d, %d, %r, %r
+m = omesh.Mesh(dim, (3,) * dim, lvl)
+B = basis.Basis(order)
+c = workloads.sphere_center(0.0)[:dim]
+u = np.zeros((len(m.cells), 1) + (2,) * dim)
+for _ in range(lvl):
+    u = m.remesh(u, omesh.sphere_flags(m, c, max(radius, 0.2)), basis.Basis(1))
+X = m.node_coords(B.xi)
+u = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X, sigma=0.15), 0, 1))
+P = opde.Euler(dim)
+h = m.cell_widths()
+dt = ader.cfl_dt(u, h, P, order, cfl=workloads.ADER_CFL[order])
+steps, t0 = 0, time.perf_counter()
+while True:
+    out = ostep.step(m, u, dt, P, B)
+    u, dt = out.u, out.dt_next
+    steps += 1
+    if time.perf_counter() - t0 > budget:
+        break
+el = time.perf_counter() - t0
+dofs = len(m.cells) * (dim + 2) * (order + 1) ** dim
+print(json.dumps(dict(value=dofs * steps / el, cells=len(m.cells), steps=steps, seconds=el)))
+""" % (ROOT, wl["dim"], wl["order"], wl["max_level"], wl["radius"], seconds)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": res["value"], "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{res['steps']} oracle steps of the same PDE/order/AMR rule on a base-3^"
+                      f"{wl['dim']} mesh with {res['cells']} cells ({res['seconds']:.1f} s, "
+                      "numpy FP64, 1 BLAS thread)"}
+
+
+def reference_arm(args, wl_name, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(wl_name, wl, seconds=2.0)
+    samples = []
+    for _ in range(args.steps):
+        r = cpu_baseline(wl_name, wl, seconds=5.0)
+        if "value" not in r:
+            print(json.dumps({"impl": "reference", "unavailable": r.get("error", "oracle failed")}))
+            return
+        vals.append(r["value"])
+        samples.append(r)
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl_name, "order": wl["order"], "dim": wl["dim"]},
+            "cpu_baseline": {"value": v, "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": v, "unit": "DoF-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="euler3d-n5-amr", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, args.workload, wl)
+        return
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    s, u0 = build_problem(wl, args.precision, device)
+    u_dev = torch.from_numpy(u0).to(device)
+    s.set_state(u_dev)
+    s.compute_dt()
+    t_dev = torch.zeros(1, dtype=torch.float64, device=device)
+    run_steps(s, wl, args.warmup, t_dev, 0)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region -----------------------------------
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = s.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dofs = run_steps(s, wl, args.steps, t_dev, args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = s.launch_count() - launches0
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    status = s.status()
+    if world > 1:
+        tt = torch.tensor([elapsed, float(dofs)], dtype=torch.float64, device=device)
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = tt.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        elapsed, total_dofs = float(mx[0]), float(sm[1])
+    else:
+        total_dofs = float(dofs)
+    value = total_dofs / elapsed
+
+    # ---- dominant kernel: the fused predictor ------------------------------
+    t_pred = time_predictor(s, torch)
+    iters = s.order + 1
+    flops = predictor_flops_per_cell(s.dim, s.order, iters, s.nvar) * s.ncells
+    bytes_ = predictor_bytes_per_cell(s.dim, s.order, s.nvar) * s.ncells
+    peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
+    achieved = flops / t_pred / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"predict_kernel<{s.dim},{s.order},Euler,"
+                          f"{'double' if args.precision == 'fp64' else 'float'}>",
+                "launch_ms": t_pred * 1e3, "algorithmic_flops": flops,
+                "algorithmic_bytes": bytes_, "hbm_gbs": bytes_ / t_pred / 1e9}
+
+    # ---- end to end through the public API with host buffers ---------------
+    # Every step: H2D of the state from pinned host memory, one step, D2H of
+    # the new state into pinned host memory (the step's result).
+    from paper_1806_07984_gb300 import ader as A
+    e2e_steps = max(2, min(args.steps, 5))
+    s.close()
+    del u_dev
+    s2, u02 = build_problem(wl, args.precision, device)
+    host = torch.from_numpy(u02).pin_memory()
+    del u02
+    s2.set_state(host)
+    s2.compute_dt()
+    torch.cuda.synchronize()
+    t_e2e = torch.zeros(1, dtype=torch.float64, device=device)
+    c0 = time.perf_counter()
+    e2e_dofs = h2d = d2h = 0
+    for i in range(e2e_steps):
+        s2.set_state(host)
+        h2d += host.numel() * 8
+        e2e_dofs += run_steps(s2, wl, 1, t_e2e, i)
+        if tuple(host.shape) != s2.state_shape():
+            host = torch.empty(s2.state_shape(), dtype=torch.float64).pin_memory()
+        A.ader_get_state(s2.ctx, host.data_ptr(), False, stream.cuda_stream)
+        d2h += host.numel() * 8
+    torch.cuda.synchronize()
+    e2e_time = time.perf_counter() - c0
+    if world > 1:
+        tt = torch.tensor([e2e_time], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_time = float(tt[0])
+    e2e = {"value": e2e_dofs * world / e2e_time, "unit": "DoF-updates/s",
+           "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+           "steps": e2e_steps}
+    ncells, dofs_now, order, dim = s2.ncells, dofs_of(s2), s2.order, s2.dim
+    s2.close()
+
+    line = {"metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "dim": dim, "order": order,
+                       "cells": ncells, "dofs": dofs_now, "precision": args.precision,
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
+                       "remesh_every": wl["remesh_every"]},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, wl)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

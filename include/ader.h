@@ -1,0 +1,220 @@
+/*
+ * ader.h - C ABI of the GB300 ADER-DG step library (libader.so).
+ *
+ * One explicit ADER-DG time step on a dynamically adaptive 3^d spacetree
+ * Cartesian mesh (Charrier, Hazelwood, Weinzierl, "Enclave Tasking for DG
+ * Methods on Dynamically Adaptive Meshes"):
+ *   - the PDE is the first-order balance law of Eq. (1) with S = 0, delta = 0;
+ *   - one step is Q(T+dT) = (C_Corr o F_R o id|dc + id|T+dT) o C_STP Q(T),
+ *     Eq. (3) and Algorithm 1: a space-time predictor per cell, Riemann solves
+ *     per face, a corrector per cell;
+ *   - at a resolution transition (Sec. 2.2) coarse predictor data are
+ *     interpolated to virtual child faces, Riemann is solved on the child
+ *     faces only, and the results are restricted into the parent face;
+ *   - dynamic adaptivity (Sec. 2.2) refines/coarsens cells between steps;
+ *   - enclave tasking (Sec. 3) becomes a skeleton batch (cells at resolution
+ *     transitions or flagged for refinement) on a high-priority CUDA stream and
+ *     an enclave batch on a low-priority stream.
+ *
+ * Conventions for every entry point:
+ *   - Returns an ader_status; never aborts or throws.  A CUDA failure returns
+ *     ADER_ERR_CUDA and ader_last_error() describes it.
+ *   - Device work is enqueued asynchronously.  `stream` arguments are
+ *     cudaStream_t handles passed as void* (NULL = the legacy default stream);
+ *     the call is ordered after earlier work on that stream and later work on
+ *     it sees its results.
+ *   - The context owns every device buffer (solution, face data, lists).
+ *     Caller pointers are borrowed for the duration of the call (host pointers)
+ *     or until the enqueued work completes (device pointers).
+ *   - dt lives in device memory (a double* from the caller): kernels read it
+ *     there, so a step needs no host synchronisation.
+ *   - Numerical failures inside kernels (non-finite predictor output, rho <= 0
+ *     or p <= 0, non-finite CFL rate) set bits of a device status word that
+ *     ader_status_word() reads after synchronising.
+ *
+ * Data layout (FP64 throughout at the boundary; c = cell, m = nvar,
+ * n = order + 1 Gauss-Legendre nodes per direction, node index with x fastest,
+ * NF = n^(dim-1) face nodes with the lowest tangential direction fastest):
+ *   state   u[c][var][node]             c in mesh order (ader_mesh_cells)
+ *   faces   X[c][2*dir + side][var][fnode]  side 0: face at xi_dir = 0
+ * Euler variables: rho, rho v_1..rho v_dim, E.  Acoustics: p, v_1..v_dim.
+ */
+#ifndef ADER_H_
+#define ADER_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ADER_OK = 0,
+  ADER_ERR_ARG = -1,          /* invalid argument or unsupported configuration */
+  ADER_ERR_CUDA = -2,         /* a CUDA call failed (see ader_last_error) */
+  ADER_ERR_OOM = -3,          /* device allocation failed */
+  ADER_ERR_NONPHYSICAL = -4,  /* status word reported a non-physical state */
+  ADER_ERR_PICARD = -5,       /* status word reported a non-finite predictor */
+  ADER_ERR_TIMEOUT = -6,      /* reserved: a bounded device wait expired */
+  ADER_ERR_MESH = -7          /* mesh operation failed (balance, transfer) */
+} ader_status;
+
+typedef enum { ADER_EULER = 0, ADER_ACOUSTICS = 1 } ader_pde;
+
+/* Arithmetic of the predictor's contractions (Picard, time averages, face
+ * extrapolation, volume term).  Riemann, restriction, corrector, CFL
+ * reduction and the stored state are FP64 in every mode. */
+typedef enum { ADER_FP64 = 0, ADER_FP32 = 1 } ader_precision;
+
+typedef enum { ADER_ALL = 0, ADER_SKELETON = 1, ADER_ENCLAVE = 2 } ader_set;
+
+typedef enum {
+  ADER_FIELD_U = 0,       /* u(T) or u(T+dt) after ader_correct        [c][var][node] */
+  ADER_FIELD_USTAR = 1,   /* u + dt * volume term (ader_predict)       [c][var][node] */
+  ADER_FIELD_FACE_Q = 2,  /* time-averaged predictor on faces          [c][2d][var][fnode] */
+  ADER_FIELD_FACE_F = 3,  /* time-averaged normal flux on faces        [c][2d][var][fnode] */
+  ADER_FIELD_FSTAR = 4    /* Riemann flux F* (after restriction)       [c][2d][var][fnode] */
+} ader_field;
+
+typedef struct {
+  int dim;           /* 2 or 3 */
+  int order;         /* polynomial order N, 1..7 (n = N + 1 nodes per direction) */
+  int nvar;          /* must be dim + 2 (Euler) or dim + 1 (acoustics) */
+  ader_pde pde;
+  double gamma;      /* Euler ratio of specific heats */
+  double cfl;        /* dt = cfl / max_cells max_nodes sum_d lambda_d / h_d */
+  int base[3];       /* base grid cells per direction (level 0), periodic */
+  double lo[3];      /* domain box */
+  double hi[3];
+  int max_level;     /* refinement levels above the base grid, 0..6 */
+  int picard_iters;  /* Picard iterations; 0 selects order + 1 */
+  ader_precision prec;
+} ader_config;
+
+typedef struct ader_ctx ader_ctx;
+
+/* Create a context on the current CUDA device with the uniform base mesh
+ * (every cell at level 0) and a zero state.  *out receives the context. */
+ader_status ader_init(const ader_config* cfg, ader_ctx** out);
+
+/* Release every device buffer and stream of the context (synchronises). */
+void ader_destroy(ader_ctx* ctx);
+
+/* Human-readable name of a status code. */
+const char* ader_error_string(ader_status s);
+
+/* Description of the last failure in this context ("" if none). */
+const char* ader_last_error(ader_ctx* ctx);
+
+/* Mesh sizes: cells, skeleton cells, conforming faces, parent faces of
+ * resolution transitions (each split into 3^(dim-1) child faces). */
+ader_status ader_mesh_info(ader_ctx* ctx, int64_t* ncells, int64_t* nskeleton, int64_t* nconf,
+                           int64_t* nparents);
+
+/* Per cell, in mesh order: level, i_x, i_y, i_z (ncells x 4 int32, host).
+ * The cell covers [lo + i h, lo + (i + 1) h) with h = (hi - lo) / (base 3^level). */
+ader_status ader_mesh_cells(ader_ctx* ctx, int32_t* cells_out);
+
+/* Per cell, in mesh order: 1 if the cell is in the skeleton batch (host). */
+ader_status ader_mesh_skeleton(ader_ctx* ctx, uint8_t* skel_out);
+
+/* The library's Gauss-Legendre nodes on [0, 1] (order + 1 doubles, host). */
+ader_status ader_nodes(ader_ctx* ctx, double* xi_out);
+
+/* Copy the state u[c][var][node] in (set) or out (get).  on_device != 0 means
+ * `u` is a device pointer; otherwise a host pointer (pinned or pageable). */
+ader_status ader_set_state(ader_ctx* ctx, const double* u, int on_device, void* stream);
+ader_status ader_get_state(ader_ctx* ctx, double* u, int on_device, void* stream);
+
+/* Copy an intermediate field out (layouts in ader_field). */
+ader_status ader_get_field(ader_ctx* ctx, ader_field f, double* out, int on_device, void* stream);
+
+/* Global time step from the current state (global time stepping, Sec. 2.1):
+ * *dt_dev = cfl / max over cells and nodes of sum_d lambda_d(u) / h_d. */
+ader_status ader_compute_dt(ader_ctx* ctx, double* dt_dev, void* stream);
+
+/* C_STP with id|T+dT and id|dc (Eq. (3), Algorithm 1 first loop) on the cells
+ * of `set`: Picard iterations of the space-time predictor, then the time
+ * averages of the predictor and of its fluxes, their extrapolation to the 2d
+ * faces (ADER_FIELD_FACE_Q/F) and u* = u + dt * volume term (ADER_FIELD_USTAR). */
+ader_status ader_predict(ader_ctx* ctx, const double* dt_dev, ader_set set, void* stream);
+
+/* F_R (Algorithm 1 second loop) with the AMR tasks of Sec. 2.2.
+ * ADER_SKELETON: Rusanov on child faces (coarse data interpolated into the
+ * virtual cells' faces), restriction into the parent faces, and conforming
+ * faces between two skeleton cells.  ADER_ENCLAVE: the other conforming faces.
+ * ADER_ALL: both.  Needs the predictor of every cell that `set` touches. */
+ader_status ader_riemann(ader_ctx* ctx, ader_set set, void* stream);
+
+/* C_Corr (Algorithm 1 third loop) on all cells: u = u* + face lifting of F*,
+ * then *dt_next_dev = cfl / max sum_d lambda_d(u) / h_d (CTA maxima by warp
+ * shuffles, one atomicMax each).  dt_next_dev may equal dt_dev. */
+ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_dev, void* stream);
+
+/* nsteps full steps.  Each step runs the skeleton predictor, transition
+ * Riemann/restriction and skeleton conforming faces on the context's
+ * high-priority stream, the enclave predictor on its low-priority stream, then
+ * the remaining faces and the corrector after both; the step's dt is read from
+ * *dt_dev and the next dt written back to it.  Ordered after earlier work on
+ * `stream`; later work on `stream` sees the result. */
+ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
+
+/* Dynamic adaptivity (Sec. 2.2): flags per cell in mesh order (+1 refine,
+ * -1 coarsen, 0 keep).  Refines flagged cells below max_level, restores 2:1
+ * face balance by further refinement, coarsens complete families of flagged
+ * leaves whose parent stays balanced, and transfers the state (interpolation
+ * into children, L2 projection onto parents).  Synchronises the device. */
+ader_status ader_remesh(ader_ctx* ctx, const int8_t* flags);
+
+/* Skeleton batch: transition cells plus cells with flags[c] > 0 (flags may be
+ * NULL).  Host call; uploads the new lists (synchronous). */
+ader_status ader_classify(ader_ctx* ctx, const int8_t* flags);
+
+/* Geometric refinement criterion (host): +1 for cells below max_level whose
+ * box meets the ball (center, radius) in the periodic domain, -1 for cells
+ * above level 0 whose parent's box misses it, 0 otherwise. */
+ader_status ader_sphere_flags(ader_ctx* ctx, const double center[3], double radius, int8_t* flags);
+
+/* Synchronise the context's streams and return the device status word
+ * (bit 0 non-finite predictor, bit 1 non-physical state, bit 2 non-finite
+ * CFL rate, bit 3 bad transfer index); clears it. */
+ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
+
+/* Number of kernel launches this context has enqueued so far. */
+ader_status ader_launch_count(ader_ctx* ctx, int64_t* out);
+
+/* ---- Host-only mesh handle (no device needed) ---------------------------
+ * The same spacetree logic as the context's mesh (Sec. 2.2 three-partitioning,
+ * 2:1 face balance, coarsening rules, skeleton of Sec. 3.1), usable without a
+ * GPU for planning and inspection. */
+typedef struct ader_mesh ader_mesh;
+
+/* Uniform base grid base[0..dim-1] (periodic), refinement up to max_level. */
+ader_status ader_mesh_create(int dim, const int base[3], int max_level, ader_mesh** out);
+void ader_mesh_destroy(ader_mesh* mesh);
+
+/* Same flags and rules as ader_remesh, without any state transfer. */
+ader_status ader_mesh_adapt(ader_mesh* mesh, const int8_t* flags);
+
+/* Sizes as in ader_mesh_info. */
+ader_status ader_mesh_sizes(ader_mesh* mesh, int64_t* ncells, int64_t* nskeleton, int64_t* nconf,
+                            int64_t* nparents);
+
+/* Leaves (ncells x 4: level, i_x, i_y, i_z) and skeleton flags in mesh order. */
+ader_status ader_mesh_leaves(ader_mesh* mesh, int32_t* cells_out, uint8_t* skel_out);
+
+/* Faces: conf_out (nconf x 3: left cell, right cell, dir; skeleton-only faces
+ * first), parents_out (nparents x 3: coarse cell, dir, coarse side), and
+ * child_out (nparents x 3^(dim-1): fine cell of sub-face sigma). */
+ader_status ader_mesh_faces(ader_mesh* mesh, int32_t* conf_out, int32_t* parents_out,
+                            int32_t* child_out);
+
+/* Geometric criterion of ader_sphere_flags on the box [lo, hi]. */
+ader_status ader_mesh_sphere_flags(ader_mesh* mesh, const double center[3], double radius,
+                                   const double lo[3], const double hi[3], int8_t* flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADER_H_ */

@@ -1,0 +1,279 @@
+"""ctypes binding of the C ABI in include/ader.h (argument marshalling only).
+
+Every function has the name and argument order of its C counterpart and
+raises ``AderError`` on a non-zero status.  Pointers are passed as Python
+ints (device pointers, e.g. ``tensor.data_ptr()``) or numpy arrays (host
+buffers); streams as ``cudaStream_t`` ints (``torch.cuda.Stream.cuda_stream``)
+or None for the legacy default stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libader.so")
+
+ADER_OK = 0
+STATUS_NAMES = {0: "ADER_OK", -1: "ADER_ERR_ARG", -2: "ADER_ERR_CUDA", -3: "ADER_ERR_OOM",
+                -4: "ADER_ERR_NONPHYSICAL", -5: "ADER_ERR_PICARD", -6: "ADER_ERR_TIMEOUT",
+                -7: "ADER_ERR_MESH"}
+ADER_EULER, ADER_ACOUSTICS = 0, 1
+ADER_FP64, ADER_FP32 = 0, 1
+ADER_ALL, ADER_SKELETON, ADER_ENCLAVE = 0, 1, 2
+ADER_FIELD_U, ADER_FIELD_USTAR, ADER_FIELD_FACE_Q, ADER_FIELD_FACE_F, ADER_FIELD_FSTAR = range(5)
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", "ader_mesh_info",
+           "ader_mesh_cells", "ader_mesh_skeleton", "ader_nodes", "ader_set_state",
+           "ader_get_state", "ader_get_field", "ader_compute_dt", "ader_predict", "ader_riemann",
+           "ader_correct", "ader_step", "ader_remesh", "ader_classify", "ader_sphere_flags",
+           "ader_status_word", "ader_launch_count", "ader_mesh_create", "ader_mesh_destroy",
+           "ader_mesh_adapt", "ader_mesh_sizes", "ader_mesh_leaves", "ader_mesh_faces",
+           "ader_mesh_sphere_flags"]
+
+
+class AderError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {detail}".strip())
+
+
+class ader_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("nvar", ctypes.c_int),
+                ("pde", ctypes.c_int), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("base", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("max_level", ctypes.c_int),
+                ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    """Load libader.so (once); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1806_07984_gb300.build` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "ader_init": ([ctypes.POINTER(ader_config), ctypes.POINTER(_vp)], ctypes.c_int),
+        "ader_destroy": ([_vp], None),
+        "ader_error_string": ([ctypes.c_int], ctypes.c_char_p),
+        "ader_last_error": ([_vp], ctypes.c_char_p),
+        "ader_mesh_info": ([_vp, _i64p, _i64p, _i64p, _i64p], ctypes.c_int),
+        "ader_mesh_cells": ([_vp, _vp], ctypes.c_int),
+        "ader_mesh_skeleton": ([_vp, _vp], ctypes.c_int),
+        "ader_nodes": ([_vp, _vp], ctypes.c_int),
+        "ader_set_state": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_get_state": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_get_field": ([_vp, ctypes.c_int, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_compute_dt": ([_vp, _vp, _vp], ctypes.c_int),
+        "ader_predict": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_riemann": ([_vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_correct": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+        "ader_step": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_remesh": ([_vp, _vp], ctypes.c_int),
+        "ader_classify": ([_vp, _vp], ctypes.c_int),
+        "ader_sphere_flags": ([_vp, _vp, ctypes.c_double, _vp], ctypes.c_int),
+        "ader_status_word": ([_vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "ader_launch_count": ([_vp, _i64p], ctypes.c_int),
+        "ader_mesh_create": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+        "ader_mesh_destroy": ([_vp], None),
+        "ader_mesh_adapt": ([_vp, _vp], ctypes.c_int),
+        "ader_mesh_sizes": ([_vp, _i64p, _i64p, _i64p, _i64p], ctypes.c_int),
+        "ader_mesh_leaves": ([_vp, _vp, _vp], ctypes.c_int),
+        "ader_mesh_faces": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+        "ader_mesh_sphere_flags": ([_vp, _vp, ctypes.c_double, _vp, _vp, _vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _check(ctx, status, where):
+    if status != ADER_OK:
+        detail = lib().ader_last_error(ctx).decode() if ctx else ""
+        raise AderError(status, where, detail)
+
+
+def ader_init(cfg):
+    ctx = _vp()
+    _check(None, lib().ader_init(ctypes.byref(cfg), ctypes.byref(ctx)), "ader_init")
+    return ctx
+
+
+def ader_destroy(ctx):
+    lib().ader_destroy(ctx)
+
+
+def ader_error_string(status):
+    return lib().ader_error_string(status).decode()
+
+
+def ader_mesh_info(ctx):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(ctx, lib().ader_mesh_info(ctx, *[ctypes.byref(x) for x in v]), "ader_mesh_info")
+    return tuple(x.value for x in v)
+
+
+def ader_mesh_cells(ctx):
+    ncells = ader_mesh_info(ctx)[0]
+    out = np.zeros((ncells, 4), dtype=np.int32)
+    _check(ctx, lib().ader_mesh_cells(ctx, _ptr(out)), "ader_mesh_cells")
+    return out
+
+
+def ader_mesh_skeleton(ctx):
+    ncells = ader_mesh_info(ctx)[0]
+    out = np.zeros(ncells, dtype=np.uint8)
+    _check(ctx, lib().ader_mesh_skeleton(ctx, _ptr(out)), "ader_mesh_skeleton")
+    return out
+
+
+def ader_nodes(ctx, n):
+    out = np.zeros(n, dtype=np.float64)
+    _check(ctx, lib().ader_nodes(ctx, _ptr(out)), "ader_nodes")
+    return out
+
+
+def ader_set_state(ctx, u, on_device, stream=None):
+    _check(ctx, lib().ader_set_state(ctx, _ptr(u), int(on_device), stream), "ader_set_state")
+
+
+def ader_get_state(ctx, u, on_device, stream=None):
+    _check(ctx, lib().ader_get_state(ctx, _ptr(u), int(on_device), stream), "ader_get_state")
+
+
+def ader_get_field(ctx, field, out, on_device, stream=None):
+    _check(ctx, lib().ader_get_field(ctx, field, _ptr(out), int(on_device), stream),
+           "ader_get_field")
+
+
+def ader_compute_dt(ctx, dt_dev, stream=None):
+    _check(ctx, lib().ader_compute_dt(ctx, _ptr(dt_dev), stream), "ader_compute_dt")
+
+
+def ader_predict(ctx, dt_dev, which=ADER_ALL, stream=None):
+    _check(ctx, lib().ader_predict(ctx, _ptr(dt_dev), which, stream), "ader_predict")
+
+
+def ader_riemann(ctx, which=ADER_ALL, stream=None):
+    _check(ctx, lib().ader_riemann(ctx, which, stream), "ader_riemann")
+
+
+def ader_correct(ctx, dt_dev, dt_next_dev, stream=None):
+    _check(ctx, lib().ader_correct(ctx, _ptr(dt_dev), _ptr(dt_next_dev), stream), "ader_correct")
+
+
+def ader_step(ctx, nsteps, dt_dev, stream=None):
+    _check(ctx, lib().ader_step(ctx, nsteps, _ptr(dt_dev), stream), "ader_step")
+
+
+def ader_remesh(ctx, flags):
+    flags = np.ascontiguousarray(flags, dtype=np.int8)
+    _check(ctx, lib().ader_remesh(ctx, _ptr(flags)), "ader_remesh")
+
+
+def ader_classify(ctx, flags=None):
+    if flags is not None:
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+    _check(ctx, lib().ader_classify(ctx, _ptr(flags)), "ader_classify")
+
+
+def ader_sphere_flags(ctx, center, radius):
+    ncells = ader_mesh_info(ctx)[0]
+    c = np.zeros(3, dtype=np.float64)
+    c[:len(center)] = center
+    out = np.zeros(ncells, dtype=np.int8)
+    _check(ctx, lib().ader_sphere_flags(ctx, _ptr(c), float(radius), _ptr(out)),
+           "ader_sphere_flags")
+    return out
+
+
+def ader_status_word(ctx):
+    v = ctypes.c_uint32()
+    _check(ctx, lib().ader_status_word(ctx, ctypes.byref(v)), "ader_status_word")
+    return v.value
+
+
+def ader_launch_count(ctx):
+    v = ctypes.c_int64()
+    _check(ctx, lib().ader_launch_count(ctx, ctypes.byref(v)), "ader_launch_count")
+    return v.value
+
+
+# ---- host-only mesh handle -------------------------------------------------
+def ader_mesh_create(dim, base, max_level):
+    b = np.ones(3, dtype=np.int32)
+    b[:dim] = base[:dim]
+    m = _vp()
+    _check(None, lib().ader_mesh_create(dim, _ptr(b), max_level, ctypes.byref(m)),
+           "ader_mesh_create")
+    return m
+
+
+def ader_mesh_destroy(mesh):
+    lib().ader_mesh_destroy(mesh)
+
+
+def ader_mesh_adapt(mesh, flags):
+    flags = np.ascontiguousarray(flags, dtype=np.int8)
+    _check(None, lib().ader_mesh_adapt(mesh, _ptr(flags)), "ader_mesh_adapt")
+
+
+def ader_mesh_sizes(mesh):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(None, lib().ader_mesh_sizes(mesh, *[ctypes.byref(x) for x in v]), "ader_mesh_sizes")
+    return tuple(x.value for x in v)
+
+
+def ader_mesh_leaves(mesh):
+    C = ader_mesh_sizes(mesh)[0]
+    cells = np.zeros((C, 4), dtype=np.int32)
+    skel = np.zeros(C, dtype=np.uint8)
+    _check(None, lib().ader_mesh_leaves(mesh, _ptr(cells), _ptr(skel)), "ader_mesh_leaves")
+    return cells, skel
+
+
+def ader_mesh_faces(mesh, dim):
+    C, _, nconf, npar = ader_mesh_sizes(mesh)
+    conf = np.zeros((nconf, 3), dtype=np.int32)
+    par = np.zeros((npar, 3), dtype=np.int32)
+    kids = np.zeros((npar, 3 ** (dim - 1)), dtype=np.int32)
+    _check(None, lib().ader_mesh_faces(mesh, _ptr(conf), _ptr(par), _ptr(kids)),
+           "ader_mesh_faces")
+    return conf, par, kids
+
+
+def ader_mesh_sphere_flags(mesh, center, radius, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    C = ader_mesh_sizes(mesh)[0]
+    c = np.zeros(3)
+    c[:len(center)] = center
+    lo_ = np.zeros(3)
+    lo_[:len(lo)] = lo
+    hi_ = np.ones(3)
+    hi_[:len(hi)] = hi
+    out = np.zeros(C, dtype=np.int8)
+    _check(None, lib().ader_mesh_sphere_flags(mesh, _ptr(c), float(radius), _ptr(lo_), _ptr(hi_),
+                                              _ptr(out)), "ader_mesh_sphere_flags")
+    return out

@@ -1,0 +1,666 @@
+// C ABI of the ADER-DG step library: context, buffers, streams, dispatch.
+#include "../../include/ader.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "basis.h"
+#include "dispatch.h"
+#include "kernels.h"
+#include "mesh.h"
+
+using namespace ader;
+
+struct ader_ctx {
+  ader_config cfg{};
+  int n = 0, NS = 0, NF = 0, M = 0;
+  Tree tree;
+  BasisTables B{};
+  double inv_h[kMaxLevels][3]{};
+  cudaStream_t s_hi = nullptr, s_lo = nullptr;
+  cudaEvent_t ev_begin = nullptr, ev_step = nullptr, ev_lo = nullptr, ev_end = nullptr;
+  // device buffers (capacity in cells)
+  int64_t cap = 0;
+  double *u = nullptr, *ustar = nullptr, *faceQ = nullptr, *faceF = nullptr, *fstar = nullptr;
+  int8_t* level = nullptr;
+  int32_t *all_cells = nullptr, *skel_cells = nullptr, *encl_cells = nullptr;
+  ConfFace* conf = nullptr;
+  int64_t conf_cap = 0;
+  ParentFace* parents = nullptr;
+  int32_t* child_fine = nullptr;
+  int64_t par_cap = 0;
+  unsigned long long* rate = nullptr;
+  uint32_t* status = nullptr;
+  double* dt_scratch = nullptr;
+  std::string err;
+  int64_t launches = 0;
+};
+
+namespace {
+
+int64_t ipow64(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+ader_status cuda_fail(ader_ctx* c, cudaError_t e, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? ADER_ERR_OOM : ADER_ERR_CUDA;
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return cuda_fail(c, e__, what); \
+  } while (0)
+
+cudaError_t do_predict(ader_ctx* c, const PredictArgs& a, cudaStream_t s) {
+  const Precision p = c->cfg.prec == ADER_FP32 ? Precision::kFP32 : Precision::kFP64;
+  const int N = c->cfg.order;
+  c->launches += a.count > 0 ? 1 : 0;
+  if (c->cfg.pde == ADER_EULER)
+    return c->cfg.dim == 2 ? predict_euler2d(N, p, a, s) : predict_euler3d(N, p, a, s);
+  return c->cfg.dim == 2 ? predict_acoustics2d(N, p, a, s) : predict_acoustics3d(N, p, a, s);
+}
+
+cudaError_t do_faces(ader_ctx* c, int which, const RiemannArgs& a, cudaStream_t s) {
+  const int N = c->cfg.order;
+  const int64_t items = which == 0 ? a.nconf : a.nparents;
+  c->launches += items > 0 ? 1 : 0;
+  if (c->cfg.pde == ADER_EULER)
+    return c->cfg.dim == 2 ? faces_euler2d(N, which, a, s) : faces_euler3d(N, which, a, s);
+  return c->cfg.dim == 2 ? faces_acoustics2d(N, which, a, s) : faces_acoustics3d(N, which, a, s);
+}
+
+cudaError_t do_correct(ader_ctx* c, bool update, const CorrectArgs& a, cudaStream_t s) {
+  const int N = c->cfg.order;
+  c->launches += a.ncells > 0 ? 1 : 0;
+  if (c->cfg.pde == ADER_EULER)
+    return c->cfg.dim == 2 ? correct_euler2d(N, update, a, s) : correct_euler3d(N, update, a, s);
+  return c->cfg.dim == 2 ? correct_acoustics2d(N, update, a, s)
+                         : correct_acoustics3d(N, update, a, s);
+}
+
+cudaError_t do_transfer(ader_ctx* c, const TransferArgs& a, cudaStream_t s) {
+  const int N = c->cfg.order;
+  c->launches += a.ncells_new > 0 ? 1 : 0;
+  if (c->cfg.pde == ADER_EULER)
+    return c->cfg.dim == 2 ? transfer_euler2d(N, a, s) : transfer_euler3d(N, a, s);
+  return c->cfg.dim == 2 ? transfer_acoustics2d(N, a, s) : transfer_acoustics3d(N, a, s);
+}
+
+template <class T>
+cudaError_t grow(T** p, int64_t* cap, int64_t need) {
+  if (need <= *cap && *p) return cudaSuccess;
+  const int64_t nc = std::max<int64_t>(need + need / 4, 16);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * size_t(nc));
+  if (e == cudaSuccess) *cap = nc;
+  return e;
+}
+
+// Cell-sized buffers for `need` cells; u (and ustar when keep_ustar) keep
+// their contents up to the old capacity.
+ader_status ensure_cells(ader_ctx* c, int64_t need) {
+  if (need <= c->cap) return ADER_OK;
+  const int64_t nc = need + need / 4;
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
+  const size_t face_bytes = size_t(2 * c->cfg.dim) * c->M * c->NF * sizeof(double);
+  double* nu = nullptr;
+  CK(cudaMalloc(&nu, cell_bytes * size_t(nc)), "cudaMalloc u");
+  if (c->u) {
+    CK(cudaMemcpy(nu, c->u, cell_bytes * size_t(c->cap), cudaMemcpyDeviceToDevice), "copy u");
+    cudaFree(c->u);
+  }
+  c->u = nu;
+  cudaFree(c->ustar);
+  cudaFree(c->faceQ);
+  cudaFree(c->faceF);
+  cudaFree(c->fstar);
+  cudaFree(c->level);
+  cudaFree(c->all_cells);
+  cudaFree(c->skel_cells);
+  cudaFree(c->encl_cells);
+  c->ustar = c->faceQ = c->faceF = c->fstar = nullptr;
+  c->level = nullptr;
+  c->all_cells = c->skel_cells = c->encl_cells = nullptr;
+  CK(cudaMalloc(&c->ustar, cell_bytes * size_t(nc)), "cudaMalloc ustar");
+  CK(cudaMalloc(&c->faceQ, face_bytes * size_t(nc)), "cudaMalloc faceQ");
+  CK(cudaMalloc(&c->faceF, face_bytes * size_t(nc)), "cudaMalloc faceF");
+  CK(cudaMalloc(&c->fstar, face_bytes * size_t(nc)), "cudaMalloc fstar");
+  CK(cudaMalloc(&c->level, size_t(nc)), "cudaMalloc level");
+  CK(cudaMalloc(&c->all_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
+  CK(cudaMalloc(&c->skel_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
+  CK(cudaMalloc(&c->encl_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
+  c->cap = nc;
+  return ADER_OK;
+}
+
+// Upload levels, cell lists and face lists of the current tree (synchronous).
+ader_status upload_mesh(ader_ctx* c) {
+  const Tree& t = c->tree;
+  const int64_t C = int64_t(t.cells.size());
+  ader_status st = ensure_cells(c, C);
+  if (st != ADER_OK) return st;
+  std::vector<int8_t> lv(static_cast<size_t>(C));
+  std::vector<int32_t> all(static_cast<size_t>(C));
+  for (int64_t i = 0; i < C; ++i) {
+    lv[size_t(i)] = int8_t(t.cells[size_t(i)].level);
+    all[size_t(i)] = int32_t(i);
+  }
+  CK(cudaMemcpy(c->level, lv.data(), size_t(C), cudaMemcpyHostToDevice), "upload level");
+  CK(cudaMemcpy(c->all_cells, all.data(), sizeof(int32_t) * size_t(C), cudaMemcpyHostToDevice),
+     "upload cells");
+  if (!t.skel_cells.empty())
+    CK(cudaMemcpy(c->skel_cells, t.skel_cells.data(), sizeof(int32_t) * t.skel_cells.size(),
+                  cudaMemcpyHostToDevice), "upload skeleton");
+  if (!t.encl_cells.empty())
+    CK(cudaMemcpy(c->encl_cells, t.encl_cells.data(), sizeof(int32_t) * t.encl_cells.size(),
+                  cudaMemcpyHostToDevice), "upload enclave");
+  CK(grow(&c->conf, &c->conf_cap, int64_t(t.conf.size())), "cudaMalloc conf");
+  if (!t.conf.empty())
+    CK(cudaMemcpy(c->conf, t.conf.data(), sizeof(ConfFace) * t.conf.size(), cudaMemcpyHostToDevice),
+       "upload conf");
+  const int64_t S = c->cfg.dim == 3 ? 9 : 3;
+  int64_t pc_old = c->par_cap;
+  CK(grow(&c->parents, &c->par_cap, int64_t(t.parents.size())), "cudaMalloc parents");
+  if (c->par_cap != pc_old || !c->child_fine) {
+    cudaFree(c->child_fine);
+    c->child_fine = nullptr;
+    CK(cudaMalloc(&c->child_fine, sizeof(int32_t) * size_t(c->par_cap * S)), "cudaMalloc children");
+  }
+  if (!t.parents.empty()) {
+    CK(cudaMemcpy(c->parents, t.parents.data(), sizeof(ParentFace) * t.parents.size(),
+                  cudaMemcpyHostToDevice), "upload parents");
+    CK(cudaMemcpy(c->child_fine, t.child_fine.data(), sizeof(int32_t) * t.child_fine.size(),
+                  cudaMemcpyHostToDevice), "upload children");
+  }
+  return ADER_OK;
+}
+
+PredictArgs predict_args(ader_ctx* c, const double* dt, ader_set set) {
+  PredictArgs a{};
+  a.u = c->u;
+  a.ustar = c->ustar;
+  a.faceQ = c->faceQ;
+  a.faceF = c->faceF;
+  if (set == ADER_SKELETON) {
+    a.cells = c->skel_cells;
+    a.count = int64_t(c->tree.skel_cells.size());
+  } else if (set == ADER_ENCLAVE) {
+    a.cells = c->encl_cells;
+    a.count = int64_t(c->tree.encl_cells.size());
+  } else {
+    a.cells = c->all_cells;
+    a.count = int64_t(c->tree.cells.size());
+  }
+  a.level = c->level;
+  a.dt = dt;
+  a.gamma = c->cfg.gamma;
+  a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  a.status = c->status;
+  std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
+  a.B = c->B;
+  return a;
+}
+
+RiemannArgs riemann_args(ader_ctx* c) {
+  RiemannArgs a{};
+  a.faceQ = c->faceQ;
+  a.faceF = c->faceF;
+  a.fstar = c->fstar;
+  a.parents = c->parents;
+  a.child_fine = c->child_fine;
+  a.nparents = int64_t(c->tree.parents.size());
+  a.gamma = c->cfg.gamma;
+  a.status = c->status;
+  a.B = c->B;
+  return a;
+}
+
+CorrectArgs correct_args(ader_ctx* c, const double* dt) {
+  CorrectArgs a{};
+  a.ustar = c->ustar;
+  a.fstar = c->fstar;
+  a.u = c->u;
+  a.level = c->level;
+  a.ncells = int64_t(c->tree.cells.size());
+  a.dt = dt;
+  a.rate_max = c->rate;
+  a.gamma = c->cfg.gamma;
+  a.status = c->status;
+  std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
+  a.B = c->B;
+  return a;
+}
+
+ader_status enqueue_riemann(ader_ctx* c, ader_set set, cudaStream_t s) {
+  RiemannArgs a = riemann_args(c);
+  const Tree& t = c->tree;
+  if (set == ADER_ALL || set == ADER_SKELETON) {
+    CK(do_faces(c, 1, a, s), "riemann child faces");
+    CK(do_faces(c, 2, a, s), "restriction");
+  }
+  if (set == ADER_SKELETON) {
+    a.conf = c->conf;
+    a.nconf = t.n_conf_skeleton;
+  } else if (set == ADER_ENCLAVE) {
+    a.conf = c->conf + t.n_conf_skeleton;
+    a.nconf = int64_t(t.conf.size()) - t.n_conf_skeleton;
+  } else {
+    a.conf = c->conf;
+    a.nconf = int64_t(t.conf.size());
+  }
+  a.nparents = 0;
+  CK(do_faces(c, 0, a, s), "riemann conforming faces");
+  return ADER_OK;
+}
+
+ader_status enqueue_correct(ader_ctx* c, const double* dt, double* dt_next, cudaStream_t s) {
+  CorrectArgs a = correct_args(c, dt);
+  CK(do_correct(c, true, a, s), "corrector");
+  c->launches += 1;
+  CK(launch_finalize_dt(c->rate, c->cfg.cfl, dt_next, c->status, s), "finalize dt");
+  return ADER_OK;
+}
+
+bool valid_config(const ader_config* cfg, std::string* why) {
+  if (cfg->dim != 2 && cfg->dim != 3) return *why = "dim must be 2 or 3", false;
+  if (cfg->order < 1 || cfg->order > 7) return *why = "order must be in 1..7", false;
+  if (cfg->pde != ADER_EULER && cfg->pde != ADER_ACOUSTICS) return *why = "unknown pde", false;
+  const int m = cfg->pde == ADER_EULER ? cfg->dim + 2 : cfg->dim + 1;
+  if (cfg->nvar != m) return *why = "nvar does not match the pde", false;
+  if (cfg->max_level < 0 || cfg->max_level > kMaxLevels - 2) return *why = "max_level out of range", false;
+  if (cfg->prec != ADER_FP64 && cfg->prec != ADER_FP32) return *why = "unknown precision", false;
+  if (!(cfg->cfl > 0.0)) return *why = "cfl must be positive", false;
+  for (int d = 0; d < cfg->dim; ++d) {
+    if (cfg->base[d] < 1) return *why = "base must be >= 1", false;
+    if (!(cfg->hi[d] > cfg->lo[d])) return *why = "empty domain", false;
+    int64_t cells = cfg->base[d];
+    for (int l = 0; l < cfg->max_level; ++l) cells *= 3;
+    if (cells >= (1 << 20)) return *why = "grid too fine for the cell key", false;
+  }
+  if (cfg->picard_iters < 0) return *why = "picard_iters must be >= 0", false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ader_error_string(ader_status s) {
+  switch (s) {
+    case ADER_OK: return "ok";
+    case ADER_ERR_ARG: return "invalid argument";
+    case ADER_ERR_CUDA: return "CUDA error";
+    case ADER_ERR_OOM: return "out of device memory";
+    case ADER_ERR_NONPHYSICAL: return "non-physical state";
+    case ADER_ERR_PICARD: return "non-finite predictor";
+    case ADER_ERR_TIMEOUT: return "device wait timed out";
+    case ADER_ERR_MESH: return "mesh error";
+  }
+  return "unknown status";
+}
+
+const char* ader_last_error(ader_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ader_status ader_init(const ader_config* cfg, ader_ctx** out) {
+  if (!cfg || !out) return ADER_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  if (!valid_config(cfg, &why)) return ADER_ERR_ARG;
+  ader_ctx* c = new ader_ctx();
+  c->cfg = *cfg;
+  for (int d = cfg->dim; d < 3; ++d) {
+    c->cfg.base[d] = 1;
+    c->cfg.lo[d] = 0.0;
+    c->cfg.hi[d] = 1.0;
+  }
+  c->n = cfg->order + 1;
+  c->NS = int(ipow64(c->n, cfg->dim));
+  c->NF = int(ipow64(c->n, cfg->dim - 1));
+  c->M = cfg->nvar;
+  make_basis(c->n, &c->B);
+  for (int l = 0; l < kMaxLevels; ++l)
+    for (int d = 0; d < 3; ++d)
+      c->inv_h[l][d] = d < cfg->dim ? double(ipow64(3, l) * c->cfg.base[d]) /
+                                          (c->cfg.hi[d] - c->cfg.lo[d])
+                                    : 0.0;
+  c->tree = Tree(cfg->dim, c->cfg.base, cfg->max_level);
+  if (!c->tree.build()) {
+    delete c;
+    return ADER_ERR_MESH;
+  }
+  ader_status st = ADER_OK;
+  auto fail = [&](ader_status s) {
+    ader_destroy(c);
+    return s;
+  };
+  int lo_prio = 0, hi_prio = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) return fail(ADER_ERR_CUDA);
+  if (cudaStreamCreateWithPriority(&c->s_hi, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->s_lo, cudaStreamNonBlocking, lo_prio) != cudaSuccess)
+    return fail(ADER_ERR_CUDA);
+  for (cudaEvent_t* e : {&c->ev_begin, &c->ev_step, &c->ev_lo, &c->ev_end})
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return fail(ADER_ERR_CUDA);
+  if (cudaMalloc(&c->rate, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&c->status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->dt_scratch, sizeof(double)) != cudaSuccess)
+    return fail(ADER_ERR_OOM);
+  if (cudaMemset(c->rate, 0, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(uint32_t)) != cudaSuccess)
+    return fail(ADER_ERR_CUDA);
+  st = upload_mesh(c);
+  if (st != ADER_OK) return fail(st);
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
+  if (cudaMemset(c->u, 0, cell_bytes * c->tree.cells.size()) != cudaSuccess) return fail(ADER_ERR_CUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(ADER_ERR_CUDA);
+  *out = c;
+  return ADER_OK;
+}
+
+void ader_destroy(ader_ctx* c) {
+  if (!c) return;
+  if (c->s_hi) cudaStreamSynchronize(c->s_hi);
+  if (c->s_lo) cudaStreamSynchronize(c->s_lo);
+  for (void* p : {(void*)c->u, (void*)c->ustar, (void*)c->faceQ, (void*)c->faceF, (void*)c->fstar,
+                  (void*)c->level, (void*)c->all_cells, (void*)c->skel_cells, (void*)c->encl_cells,
+                  (void*)c->conf, (void*)c->parents, (void*)c->child_fine, (void*)c->rate,
+                  (void*)c->status, (void*)c->dt_scratch})
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : {c->ev_begin, c->ev_step, c->ev_lo, c->ev_end})
+    if (e) cudaEventDestroy(e);
+  if (c->s_hi) cudaStreamDestroy(c->s_hi);
+  if (c->s_lo) cudaStreamDestroy(c->s_lo);
+  delete c;
+}
+
+ader_status ader_mesh_info(ader_ctx* c, int64_t* ncells, int64_t* nskel, int64_t* nconf,
+                           int64_t* nparents) {
+  if (!c) return ADER_ERR_ARG;
+  if (ncells) *ncells = int64_t(c->tree.cells.size());
+  if (nskel) *nskel = int64_t(c->tree.skel_cells.size());
+  if (nconf) *nconf = int64_t(c->tree.conf.size());
+  if (nparents) *nparents = int64_t(c->tree.parents.size());
+  return ADER_OK;
+}
+
+ader_status ader_mesh_cells(ader_ctx* c, int32_t* out) {
+  if (!c || !out) return ADER_ERR_ARG;
+  for (size_t i = 0; i < c->tree.cells.size(); ++i) {
+    const Key& k = c->tree.cells[i];
+    out[4 * i + 0] = k.level;
+    out[4 * i + 1] = k.x[0];
+    out[4 * i + 2] = k.x[1];
+    out[4 * i + 3] = k.x[2];
+  }
+  return ADER_OK;
+}
+
+ader_status ader_mesh_skeleton(ader_ctx* c, uint8_t* out) {
+  if (!c || !out) return ADER_ERR_ARG;
+  std::memcpy(out, c->tree.skeleton.data(), c->tree.skeleton.size());
+  return ADER_OK;
+}
+
+ader_status ader_nodes(ader_ctx* c, double* xi) {
+  if (!c || !xi) return ADER_ERR_ARG;
+  for (int i = 0; i < c->n; ++i) xi[i] = c->B.xi[i];
+  return ADER_OK;
+}
+
+static ader_status copy_cells(ader_ctx* c, double* dst, const double* src, size_t bytes, int on_device,
+                              bool to_device, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                  : (to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  CK(cudaMemcpyAsync(dst, src, bytes, kind, s), "state copy");
+  if (!on_device) CK(cudaStreamSynchronize(s), "state copy sync");
+  return ADER_OK;
+}
+
+ader_status ader_set_state(ader_ctx* c, const double* u, int on_device, void* stream) {
+  if (!c || !u) return ADER_ERR_ARG;
+  const size_t bytes = size_t(c->M) * c->NS * sizeof(double) * c->tree.cells.size();
+  return copy_cells(c, c->u, u, bytes, on_device, true, stream);
+}
+
+ader_status ader_get_state(ader_ctx* c, double* u, int on_device, void* stream) {
+  if (!c || !u) return ADER_ERR_ARG;
+  const size_t bytes = size_t(c->M) * c->NS * sizeof(double) * c->tree.cells.size();
+  return copy_cells(c, u, c->u, bytes, on_device, false, stream);
+}
+
+ader_status ader_get_field(ader_ctx* c, ader_field f, double* out, int on_device, void* stream) {
+  if (!c || !out) return ADER_ERR_ARG;
+  const size_t C = c->tree.cells.size();
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double) * C;
+  const size_t face_bytes = size_t(2 * c->cfg.dim) * c->M * c->NF * sizeof(double) * C;
+  switch (f) {
+    case ADER_FIELD_U: return copy_cells(c, out, c->u, cell_bytes, on_device, false, stream);
+    case ADER_FIELD_USTAR: return copy_cells(c, out, c->ustar, cell_bytes, on_device, false, stream);
+    case ADER_FIELD_FACE_Q: return copy_cells(c, out, c->faceQ, face_bytes, on_device, false, stream);
+    case ADER_FIELD_FACE_F: return copy_cells(c, out, c->faceF, face_bytes, on_device, false, stream);
+    case ADER_FIELD_FSTAR: return copy_cells(c, out, c->fstar, face_bytes, on_device, false, stream);
+  }
+  return ADER_ERR_ARG;
+}
+
+ader_status ader_compute_dt(ader_ctx* c, double* dt_dev, void* stream) {
+  if (!c || !dt_dev) return ADER_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CorrectArgs a = correct_args(c, nullptr);
+  CK(do_correct(c, false, a, s), "rate");
+  c->launches += 1;
+  CK(launch_finalize_dt(c->rate, c->cfg.cfl, dt_dev, c->status, s), "finalize dt");
+  return ADER_OK;
+}
+
+ader_status ader_predict(ader_ctx* c, const double* dt_dev, ader_set set, void* stream) {
+  if (!c || !dt_dev) return ADER_ERR_ARG;
+  PredictArgs a = predict_args(c, dt_dev, set);
+  CK(do_predict(c, a, static_cast<cudaStream_t>(stream)), "predictor");
+  return ADER_OK;
+}
+
+ader_status ader_riemann(ader_ctx* c, ader_set set, void* stream) {
+  if (!c) return ADER_ERR_ARG;
+  return enqueue_riemann(c, set, static_cast<cudaStream_t>(stream));
+}
+
+ader_status ader_correct(ader_ctx* c, const double* dt_dev, double* dt_next_dev, void* stream) {
+  if (!c || !dt_dev || !dt_next_dev) return ADER_ERR_ARG;
+  return enqueue_correct(c, dt_dev, dt_next_dev, static_cast<cudaStream_t>(stream));
+}
+
+ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
+  if (!c || !dt_dev || nsteps < 0) return ADER_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaEventRecord(c->ev_begin, s), "event");
+  CK(cudaStreamWaitEvent(c->s_hi, c->ev_begin, 0), "event");
+  for (int k = 0; k < nsteps; ++k) {
+    CK(cudaEventRecord(c->ev_step, c->s_hi), "event");
+    CK(cudaStreamWaitEvent(c->s_lo, c->ev_step, 0), "event");
+    PredictArgs ps = predict_args(c, dt_dev, ADER_SKELETON);
+    CK(do_predict(c, ps, c->s_hi), "skeleton predictor");
+    ader_status st = enqueue_riemann(c, ADER_SKELETON, c->s_hi);
+    if (st != ADER_OK) return st;
+    PredictArgs pe = predict_args(c, dt_dev, ADER_ENCLAVE);
+    CK(do_predict(c, pe, c->s_lo), "enclave predictor");
+    CK(cudaEventRecord(c->ev_lo, c->s_lo), "event");
+    CK(cudaStreamWaitEvent(c->s_hi, c->ev_lo, 0), "event");
+    st = enqueue_riemann(c, ADER_ENCLAVE, c->s_hi);
+    if (st != ADER_OK) return st;
+    st = enqueue_correct(c, dt_dev, dt_dev, c->s_hi);
+    if (st != ADER_OK) return st;
+  }
+  CK(cudaEventRecord(c->ev_end, c->s_hi), "event");
+  CK(cudaStreamWaitEvent(s, c->ev_end, 0), "event");
+  return ADER_OK;
+}
+
+ader_status ader_classify(ader_ctx* c, const int8_t* flags) {
+  if (!c) return ADER_ERR_ARG;
+  CK(cudaDeviceSynchronize(), "sync before classify");
+  c->tree.classify(flags);
+  return upload_mesh(c);
+}
+
+ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
+  if (!c || !flags) return ADER_ERR_ARG;
+  CK(cudaDeviceSynchronize(), "sync before remesh");
+  const int64_t C_old = int64_t(c->tree.cells.size());
+  std::vector<TransferItem> plan;
+  std::vector<int32_t> kids;
+  if (!c->tree.remesh(flags, &plan, &kids)) {
+    c->err = c->tree.error();
+    return ADER_ERR_MESH;
+  }
+  const int64_t C_new = int64_t(c->tree.cells.size());
+  // keep the old state while the cell-sized buffers grow
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
+  double* old_u = nullptr;
+  CK(cudaMalloc(&old_u, cell_bytes * size_t(std::max<int64_t>(C_old, 1))), "cudaMalloc remesh");
+  CK(cudaMemcpy(old_u, c->u, cell_bytes * size_t(C_old), cudaMemcpyDeviceToDevice), "copy u");
+  ader_status st = upload_mesh(c);
+  if (st != ADER_OK) {
+    cudaFree(old_u);
+    return st;
+  }
+  TransferItem* d_plan = nullptr;
+  int32_t* d_kids = nullptr;
+  CK(cudaMalloc(&d_plan, sizeof(TransferItem) * plan.size()), "cudaMalloc plan");
+  CK(cudaMalloc(&d_kids, sizeof(int32_t) * std::max<size_t>(kids.size(), 1)), "cudaMalloc kids");
+  CK(cudaMemcpy(d_plan, plan.data(), sizeof(TransferItem) * plan.size(), cudaMemcpyHostToDevice),
+     "upload plan");
+  if (!kids.empty())
+    CK(cudaMemcpy(d_kids, kids.data(), sizeof(int32_t) * kids.size(), cudaMemcpyHostToDevice),
+       "upload kids");
+  TransferArgs a{};
+  a.u_old = old_u;
+  a.u_new = c->u;
+  a.plan = d_plan;
+  a.children = d_kids;
+  a.ncells_new = C_new;
+  a.ncells_old = C_old;
+  a.status = c->status;
+  a.B = c->B;
+  cudaError_t e = do_transfer(c, a, nullptr);
+  cudaError_t e2 = cudaDeviceSynchronize();
+  cudaFree(old_u);
+  cudaFree(d_plan);
+  cudaFree(d_kids);
+  if (e != cudaSuccess) return cuda_fail(c, e, "transfer");
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "transfer sync");
+  return ADER_OK;
+}
+
+ader_status ader_sphere_flags(ader_ctx* c, const double center[3], double radius, int8_t* flags) {
+  if (!c || !center || !flags) return ADER_ERR_ARG;
+  c->tree.sphere_flags(center, radius, c->cfg.lo, c->cfg.hi, flags);
+  return ADER_OK;
+}
+
+ader_status ader_status_word(ader_ctx* c, uint32_t* out) {
+  if (!c || !out) return ADER_ERR_ARG;
+  CK(cudaDeviceSynchronize(), "sync");
+  CK(cudaMemcpy(out, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read status");
+  CK(cudaMemset(c->status, 0, sizeof(uint32_t)), "clear status");
+  return ADER_OK;
+}
+
+ader_status ader_launch_count(ader_ctx* c, int64_t* out) {
+  if (!c || !out) return ADER_ERR_ARG;
+  *out = c->launches;
+  return ADER_OK;
+}
+
+struct ader_mesh {
+  Tree tree;
+};
+
+ader_status ader_mesh_create(int dim, const int base[3], int max_level, ader_mesh** out) {
+  if (!base || !out || (dim != 2 && dim != 3) || max_level < 0 || max_level > kMaxLevels - 2)
+    return ADER_ERR_ARG;
+  *out = nullptr;
+  int b[3] = {1, 1, 1};
+  for (int d = 0; d < dim; ++d) {
+    if (base[d] < 1) return ADER_ERR_ARG;
+    b[d] = base[d];
+  }
+  ader_mesh* m = new ader_mesh();
+  m->tree = Tree(dim, b, max_level);
+  if (!m->tree.build()) {
+    delete m;
+    return ADER_ERR_MESH;
+  }
+  *out = m;
+  return ADER_OK;
+}
+
+void ader_mesh_destroy(ader_mesh* m) { delete m; }
+
+ader_status ader_mesh_adapt(ader_mesh* m, const int8_t* flags) {
+  if (!m || !flags) return ADER_ERR_ARG;
+  std::vector<TransferItem> plan;
+  std::vector<int32_t> kids;
+  return m->tree.remesh(flags, &plan, &kids) ? ADER_OK : ADER_ERR_MESH;
+}
+
+ader_status ader_mesh_sizes(ader_mesh* m, int64_t* ncells, int64_t* nskel, int64_t* nconf,
+                            int64_t* nparents) {
+  if (!m) return ADER_ERR_ARG;
+  if (ncells) *ncells = int64_t(m->tree.cells.size());
+  if (nskel) *nskel = int64_t(m->tree.skel_cells.size());
+  if (nconf) *nconf = int64_t(m->tree.conf.size());
+  if (nparents) *nparents = int64_t(m->tree.parents.size());
+  return ADER_OK;
+}
+
+ader_status ader_mesh_leaves(ader_mesh* m, int32_t* cells_out, uint8_t* skel_out) {
+  if (!m) return ADER_ERR_ARG;
+  const Tree& t = m->tree;
+  for (size_t i = 0; i < t.cells.size(); ++i) {
+    if (cells_out) {
+      cells_out[4 * i + 0] = t.cells[i].level;
+      for (int d = 0; d < 3; ++d) cells_out[4 * i + 1 + d] = t.cells[i].x[d];
+    }
+    if (skel_out) skel_out[i] = t.skeleton[i];
+  }
+  return ADER_OK;
+}
+
+ader_status ader_mesh_faces(ader_mesh* m, int32_t* conf_out, int32_t* parents_out,
+                            int32_t* child_out) {
+  if (!m) return ADER_ERR_ARG;
+  const Tree& t = m->tree;
+  if (conf_out)
+    for (size_t i = 0; i < t.conf.size(); ++i) {
+      conf_out[3 * i + 0] = t.conf[i].left;
+      conf_out[3 * i + 1] = t.conf[i].right;
+      conf_out[3 * i + 2] = t.conf[i].dir;
+    }
+  if (parents_out)
+    for (size_t i = 0; i < t.parents.size(); ++i) {
+      parents_out[3 * i + 0] = t.parents[i].coarse;
+      parents_out[3 * i + 1] = t.parents[i].dir;
+      parents_out[3 * i + 2] = t.parents[i].coarse_side;
+    }
+  if (child_out) std::memcpy(child_out, t.child_fine.data(), sizeof(int32_t) * t.child_fine.size());
+  return ADER_OK;
+}
+
+ader_status ader_mesh_sphere_flags(ader_mesh* m, const double center[3], double radius,
+                                   const double lo[3], const double hi[3], int8_t* flags) {
+  if (!m || !center || !lo || !hi || !flags) return ADER_ERR_ARG;
+  m->tree.sphere_flags(center, radius, lo, hi, flags);
+  return ADER_OK;
+}
+
+}  // extern "C"

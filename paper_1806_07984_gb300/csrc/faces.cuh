@@ -1,0 +1,398 @@
+// Face and cell kernels after the predictor (paper Eq. (3), Algorithm 1
+// second and third loops, Sec. 2.2 interpolation/restriction):
+//
+// * riemann_conf  - F_R on conforming faces: Rusanov on time-averaged face
+//                   data, F* = (F_L + F_R)/2 - s (Q_R - Q_L)/2, one speed s per
+//                   face (max of lambda_d over the face nodes of both sides).
+// * riemann_child - the same on child faces of a resolution transition; the
+//                   coarse side is the virtual cell's face, obtained by
+//                   tangential interpolation P_s of the coarse face data.
+// * restrict      - accumulate-Riemann: parent F* = sum_sigma (R_s0 x R_s1)
+//                   F*_sigma, children summed in ascending sigma (no atomics,
+//                   deterministic).
+// * correct       - u = u* + dt sum_d h_d^-1 [lift0_{i_d} F*_{d,-} -
+//                   lift1_{i_d} F*_{d,+}] with lift = phi / w, and the CFL
+//                   rate max sum_d lambda_d / h_d by warp shuffles and one
+//                   atomicMax per CTA.
+// * transfer      - remesh volume transfer: copy, interpolate into a child,
+//                   or L2-project 3^d children onto the parent.
+// All in FP64.  Face kernels map one warp to one face (lanes over face nodes).
+#pragma once
+#include "kernels.h"
+#include "pde.cuh"
+#include "predict.cuh"
+
+namespace ader {
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ bool warp_all(bool b) { return __all_sync(0xffffffffu, b); }
+
+template <int DIM, int N, class PDE>
+__device__ __forceinline__ void rusanov_store(const double (&QL)[PDE::M], const double (&FL)[PDE::M],
+                                              const double (&QR)[PDE::M], const double (&FR)[PDE::M],
+                                              double s, double* outA, double* outB, int64_t stride) {
+#pragma unroll
+  for (int v = 0; v < PDE::M; ++v) {
+    const double F = 0.5 * (FL[v] + FR[v]) - 0.5 * s * (QR[v] - QL[v]);
+    outA[v * stride] = F;
+    if (outB) outB[v * stride] = F;
+  }
+}
+
+template <int DIM, int N, class PDE>
+__global__ void riemann_conf_kernel(const RiemannArgs a) {
+  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M, PER = (NF + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t f = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (f >= a.nconf) return;
+  const ConfFace cf = a.conf[f];
+  const int d = cf.dir;
+  const int64_t oL = (int64_t(cf.left) * 2 * DIM + 2 * d + 1) * M * NF;
+  const int64_t oR = (int64_t(cf.right) * 2 * DIM + 2 * d + 0) * M * NF;
+  double QL[PER][M], QR[PER][M];
+  double smax = 0.0;
+  bool ok = true;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int fn = lane + 32 * t;
+    if (fn < NF) {
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        QL[t][v] = a.faceQ[oL + v * NF + fn];
+        QR[t][v] = a.faceQ[oR + v * NF + fn];
+      }
+      bool o1, o2;
+      const double l1 = PDE::max_speed(QL[t], d, a.gamma, &o1);
+      const double l2 = PDE::max_speed(QR[t], d, a.gamma, &o2);
+      smax = fmax(smax, fmax(l1, l2));
+      ok = ok && o1 && o2;
+    }
+  }
+  smax = warp_max(smax);
+  if (!warp_all(ok) && lane == 0) atomicOr(a.status, kStatusNonPhysical);
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int fn = lane + 32 * t;
+    if (fn < NF) {
+      double FL[M], FR[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        FL[v] = a.faceF[oL + v * NF + fn];
+        FR[v] = a.faceF[oR + v * NF + fn];
+      }
+      rusanov_store<DIM, N, PDE>(QL[t], FL, QR[t], FR, smax, a.fstar + oL + fn, a.fstar + oR + fn,
+                                 NF);
+    }
+  }
+}
+
+// Tangential interpolation of one coarse face block onto child sub-face
+// (s0, s1) at face node (ia, ib): X_v = sum_j P[s1][ib][j] sum_i P[s0][ia][i] X(i + n j).
+template <int DIM, int N, int M>
+__device__ __forceinline__ void prolong_node(const double* X, int64_t stride, const BasisTables& B,
+                                             int s0, int s1, int ia, int ib, double (&out)[M]) {
+  constexpr int n = N + 1;
+#pragma unroll
+  for (int v = 0; v < M; ++v) out[v] = 0.0;
+  if (DIM == 2) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const double p = B.P[s0][ia][i];
+#pragma unroll
+      for (int v = 0; v < M; ++v) out[v] = fma(p, X[v * stride + i], out[v]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      double t[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) t[v] = 0.0;
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        const double p = B.P[s0][ia][i];
+#pragma unroll
+        for (int v = 0; v < M; ++v) t[v] = fma(p, X[v * stride + i + n * j], t[v]);
+      }
+      const double p1 = B.P[s1][ib][j];
+#pragma unroll
+      for (int v = 0; v < M; ++v) out[v] = fma(p1, t[v], out[v]);
+    }
+  }
+}
+
+template <int DIM, int N, class PDE>
+__global__ void riemann_child_kernel(const RiemannArgs a) {
+  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M, PER = (NF + 31) / 32;
+  constexpr int S = DIM == 3 ? 9 : 3;
+  const int lane = threadIdx.x & 31;
+  const int64_t ci = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (ci >= a.nparents * S) return;
+  const int64_t p = ci / S;
+  const int sigma = int(ci - p * S);
+  const ParentFace pf = a.parents[p];
+  const int d = pf.dir, cs = pf.coarse_side;
+  const int64_t fine = a.child_fine[ci];
+  const int64_t oC = (int64_t(pf.coarse) * 2 * DIM + 2 * d + cs) * M * NF;
+  const int64_t oF = (fine * 2 * DIM + 2 * d + (1 - cs)) * M * NF;
+  const int s0 = sigma % 3, s1 = sigma / 3;
+  double Qv[PER][M], Qf[PER][M];
+  double smax = 0.0;
+  bool ok = true;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int fn = lane + 32 * t;
+    if (fn < NF) {
+      prolong_node<DIM, N, M>(a.faceQ + oC, NF, a.B, s0, s1, fn % n, fn / n, Qv[t]);
+#pragma unroll
+      for (int v = 0; v < M; ++v) Qf[t][v] = a.faceQ[oF + v * NF + fn];
+      bool o1, o2;
+      const double l1 = PDE::max_speed(Qv[t], d, a.gamma, &o1);
+      const double l2 = PDE::max_speed(Qf[t], d, a.gamma, &o2);
+      smax = fmax(smax, fmax(l1, l2));
+      ok = ok && o1 && o2;
+    }
+  }
+  smax = warp_max(smax);
+  if (!warp_all(ok) && lane == 0) atomicOr(a.status, kStatusNonPhysical);
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int fn = lane + 32 * t;
+    if (fn < NF) {
+      double Fv[M], Ff[M];
+      prolong_node<DIM, N, M>(a.faceF + oC, NF, a.B, s0, s1, fn % n, fn / n, Fv);
+#pragma unroll
+      for (int v = 0; v < M; ++v) Ff[v] = a.faceF[oF + v * NF + fn];
+      if (cs == 1)  // coarse cell on the left
+        rusanov_store<DIM, N, PDE>(Qv[t], Fv, Qf[t], Ff, smax, a.fstar + oF + fn, nullptr, NF);
+      else
+        rusanov_store<DIM, N, PDE>(Qf[t], Ff, Qv[t], Fv, smax, a.fstar + oF + fn, nullptr, NF);
+    }
+  }
+}
+
+template <int DIM, int N, class PDE>
+__global__ void restrict_kernel(const RiemannArgs a) {
+  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M, PER = (NF + 31) / 32;
+  constexpr int S = DIM == 3 ? 9 : 3;
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (p >= a.nparents) return;
+  const ParentFace pf = a.parents[p];
+  const int d = pf.dir, cs = pf.coarse_side;
+  const int64_t oC = (int64_t(pf.coarse) * 2 * DIM + 2 * d + cs) * M * NF;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int fn = lane + 32 * t;
+    if (fn >= NF) continue;
+    const int ia = fn % n, ib = fn / n;
+    double acc[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) acc[v] = 0.0;
+    for (int sigma = 0; sigma < S; ++sigma) {
+      const int64_t fine = a.child_fine[p * S + sigma];
+      const double* X = a.fstar + (fine * 2 * DIM + 2 * d + (1 - cs)) * M * NF;
+      const int s0 = sigma % 3, s1 = sigma / 3;
+      if (DIM == 2) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          const double r = a.B.R[s0][ia][i];
+#pragma unroll
+          for (int v = 0; v < M; ++v) acc[v] = fma(r, X[v * NF + i], acc[v]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          double tt[M];
+#pragma unroll
+          for (int v = 0; v < M; ++v) tt[v] = 0.0;
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            const double r = a.B.R[s0][ia][i];
+#pragma unroll
+            for (int v = 0; v < M; ++v) tt[v] = fma(r, X[v * NF + i + n * j], tt[v]);
+          }
+          const double r1 = a.B.R[s1][ib][j];
+#pragma unroll
+          for (int v = 0; v < M; ++v) acc[v] = fma(r1, tt[v], acc[v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) a.fstar[oC + v * NF + fn] = acc[v];
+  }
+}
+
+// CTA-wide max, one atomicMax on the FP64 bit pattern (non-negative doubles
+// order like their unsigned bit patterns; NaN sorts above +inf).
+__device__ __forceinline__ void block_max_to(double v, unsigned long long* out) {
+  __shared__ double red[32];
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double x = lane < nw ? red[lane] : 0.0;
+    x = warp_max(x);
+    if (lane == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(x)));
+  }
+}
+
+template <int DIM, int N, class PDE, bool UPDATE>
+__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) correct_kernel(const CorrectArgs a) {
+  using SH = PredictShape<DIM, N>;
+  constexpr int n = SH::n, NS = SH::NS, NF = SH::NF, CPB = SH::CPB, M = PDE::M;
+  const int tid = threadIdx.x;
+  const int cl = tid / NS;
+  const int node = tid - cl * NS;
+  const int64_t cell = int64_t(blockIdx.x) * CPB + cl;
+  const bool valid = cell < a.ncells;
+  double rate = 0.0;
+  if (valid) {
+    const int id[3] = {node % n, (node / n) % n, node / (n * n)};
+    const int lv = int(a.level[cell]);
+    double q[M];
+    if (UPDATE) {
+      const double dt = *a.dt;
+      double upd[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) upd[v] = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        int fnode;
+        if (DIM == 2)
+          fnode = d == 0 ? id[1] : id[0];
+        else
+          fnode = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
+        const double* F0 = a.fstar + (cell * 2 * DIM + 2 * d + 0) * M * NF + fnode;
+        const double* F1 = a.fstar + (cell * 2 * DIM + 2 * d + 1) * M * NF + fnode;
+        const double l0 = a.B.lift0[id[d]] * a.inv_h[lv][d];
+        const double l1 = a.B.lift1[id[d]] * a.inv_h[lv][d];
+#pragma unroll
+        for (int v = 0; v < M; ++v) upd[v] = fma(l0, F0[v * NF], fma(-l1, F1[v * NF], upd[v]));
+      }
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const int64_t gi = (cell * M + v) * NS + node;
+        q[v] = fma(dt, upd[v], a.ustar[gi]);
+        a.u[gi] = q[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < M; ++v) q[v] = a.u[(cell * M + v) * NS + node];
+    }
+    bool ok_all = true;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      bool ok;
+      rate += PDE::max_speed(q, d, a.gamma, &ok) * a.inv_h[lv][d];
+      ok_all = ok_all && ok;
+    }
+    if (!ok_all) {
+      atomicOr(a.status, kStatusNonPhysical);
+      rate = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks the rate
+    }
+  }
+  block_max_to(rate, a.rate_max);
+}
+
+// Remesh transfer: one CTA per new cell, threads over the nodes, separable
+// per-axis application of P_s (refine) or R_s (coarsen) in shared memory.
+template <int DIM, int N, int M>
+__global__ void __launch_bounds__(PredictShape<DIM, N>::NS) transfer_kernel(const TransferArgs a) {
+  constexpr int n = N + 1, NS = ipow(n, DIM);
+  __shared__ double bufA[M * NS], bufB[M * NS];
+  const int64_t c = blockIdx.x;
+  if (c >= a.ncells_new) return;
+  const TransferItem it = a.plan[c];
+  const int node = threadIdx.x;
+  const int id[3] = {node % n, (node / n) % n, node / (n * n)};
+  const int stride[3] = {1, n, n * n};
+  double acc[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) acc[v] = 0.0;
+  const int nsrc = it.kind == 2 ? ipow(3, DIM) : 1;
+  for (int k = 0; k < nsrc; ++k) {
+    int64_t src = it.kind == 2 ? int64_t(a.children[it.src + k]) : int64_t(it.src);
+    if (src < 0 || src >= a.ncells_old) {
+      if (node == 0) atomicOr(a.status, kStatusBadTransfer);
+      src = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < M; ++v) bufA[v * NS + node] = a.u_old[(src * M + v) * NS + node];
+    __syncthreads();
+    if (it.kind == 0) {
+#pragma unroll
+      for (int v = 0; v < M; ++v) acc[v] = bufA[v * NS + node];
+      continue;
+    }
+    int s[3];
+    const int sc = it.kind == 1 ? it.child : k;
+    s[0] = sc % 3;
+    s[1] = (sc / 3) % 3;
+    s[2] = sc / 9;
+    double* in = bufA;
+    double* out = bufB;
+    for (int d = 0; d < DIM; ++d) {
+      const int base = node - id[d] * stride[d];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          const double m = it.kind == 1 ? a.B.P[s[d]][id[d]][j] : a.B.R[s[d]][id[d]][j];
+          t = fma(m, in[v * NS + base + j * stride[d]], t);
+        }
+        out[v * NS + node] = t;
+      }
+      __syncthreads();
+      double* tmp = in;
+      in = out;
+      out = tmp;
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) acc[v] += in[v * NS + node];
+  }
+#pragma unroll
+  for (int v = 0; v < M; ++v) a.u_new[(c * M + v) * NS + node] = acc[v];
+}
+
+template <int DIM, int N, class PDE>
+cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
+  constexpr int S = DIM == 3 ? 9 : 3;
+  const int threads = 128;
+  int64_t items = which == 0 ? a.nconf : (which == 1 ? a.nparents * S : a.nparents);
+  if (items == 0) return cudaSuccess;
+  const int64_t blocks = (items * 32 + threads - 1) / threads;
+  if (which == 0)
+    riemann_conf_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
+  else if (which == 1)
+    riemann_child_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
+  else
+    restrict_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, class PDE, bool UPDATE>
+cudaError_t launch_correct_t(const CorrectArgs& a, cudaStream_t s) {
+  using SH = PredictShape<DIM, N>;
+  if (a.ncells == 0) return cudaSuccess;
+  const int64_t blocks = (a.ncells + SH::CPB - 1) / SH::CPB;
+  correct_kernel<DIM, N, PDE, UPDATE><<<unsigned(blocks), SH::THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int M>
+cudaError_t launch_transfer_t(const TransferArgs& a, cudaStream_t s) {
+  if (a.ncells_new == 0) return cudaSuccess;
+  transfer_kernel<DIM, N, M><<<unsigned(a.ncells_new), ipow(N + 1, DIM), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ader

@@ -1,0 +1,3 @@
+// Kernels for Acoustics<2> (orders 1..7).
+#include "instantiate.cuh"
+ADER_INSTANTIATE(acoustics2d, 2, ader::Acoustics<2>)

@@ -1,0 +1,3 @@
+// Kernels for Acoustics<3> (orders 1..7).
+#include "instantiate.cuh"
+ADER_INSTANTIATE(acoustics3d, 3, ader::Acoustics<3>)

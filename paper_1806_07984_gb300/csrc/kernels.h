@@ -1,0 +1,98 @@
+// Argument blocks and launch entry points of the ADER-DG device kernels.
+//
+// Device data layout (all FP64, cell index c, m variables, n = N + 1 nodes
+// per direction, node index x fastest, NF = n^(d-1) face nodes with the
+// lowest tangential direction fastest):
+//   u, ustar      [c][var][node]
+//   faceQ, faceF  [c][2 * dir + side][var][fnode]   (side 0: xi_dir = 0)
+//   fstar         [c][2 * dir + side][var][fnode]
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "basis.h"
+#include "mesh.h"
+
+namespace ader {
+
+constexpr int kMaxLevels = 8;
+
+enum StatusBits : uint32_t {
+  kStatusNonFinitePredictor = 1u,
+  kStatusNonPhysical = 2u,
+  kStatusNonFiniteRate = 4u,
+  kStatusBadTransfer = 8u,
+};
+
+struct PredictArgs {
+  const double* u;
+  double* ustar;
+  double* faceQ;
+  double* faceF;
+  const int32_t* cells;  // cells to process (count entries)
+  int64_t count;
+  const int8_t* level;   // per cell
+  const double* dt;      // device scalar
+  double gamma;
+  int iters;             // Picard iterations
+  uint32_t* status;
+  double inv_h[kMaxLevels][3];
+  BasisTables B;
+};
+
+struct RiemannArgs {
+  const double* faceQ;
+  const double* faceF;
+  double* fstar;
+  const ConfFace* conf;       // conforming faces to solve
+  int64_t nconf;
+  const ParentFace* parents;  // transitions
+  const int32_t* child_fine;  // [parent * 3^(d-1) + sigma]
+  int64_t nparents;
+  double gamma;
+  uint32_t* status;
+  BasisTables B;
+};
+
+struct CorrectArgs {
+  const double* ustar;
+  const double* fstar;
+  double* u;
+  const int8_t* level;
+  int64_t ncells;
+  const double* dt;
+  unsigned long long* rate_max;  // max over nodes of sum_d lambda_d / h_d (as FP64 bits)
+  double gamma;
+  uint32_t* status;
+  double inv_h[kMaxLevels][3];
+  BasisTables B;
+};
+
+struct TransferArgs {
+  const double* u_old;
+  double* u_new;
+  const TransferItem* plan;
+  const int32_t* children;  // coarsening: 3^d old cells per item, lexicographic s
+  int64_t ncells_new;
+  int64_t ncells_old;
+  uint32_t* status;
+  BasisTables B;
+};
+
+enum class Precision { kFP64 = 0, kFP32 = 1 };
+
+// Returns cudaErrorInvalidValue when (dim, order, pde, precision) has no
+// compiled kernel.
+cudaError_t launch_predict(int dim, int order, int pde, Precision prec, const PredictArgs& a,
+                           cudaStream_t s);
+cudaError_t launch_riemann_conf(int dim, int order, int pde, const RiemannArgs& a, cudaStream_t s);
+cudaError_t launch_riemann_child(int dim, int order, int pde, const RiemannArgs& a, cudaStream_t s);
+cudaError_t launch_restrict(int dim, int order, int pde, const RiemannArgs& a, cudaStream_t s);
+cudaError_t launch_correct(int dim, int order, int pde, const CorrectArgs& a, cudaStream_t s);
+cudaError_t launch_rate(int dim, int order, int pde, const CorrectArgs& a, cudaStream_t s);
+cudaError_t launch_finalize_dt(unsigned long long* rate_max, double cfl, double* dt_next,
+                               uint32_t* status, cudaStream_t s);
+cudaError_t launch_transfer(int dim, int order, int nvar, const TransferArgs& a, cudaStream_t s);
+
+}  // namespace ader

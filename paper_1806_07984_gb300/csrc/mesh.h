@@ -1,0 +1,118 @@
+// Host-side 3^d spacetree: leaves, face lists, skeleton/enclave split and
+// remeshing plans for the ADER-DG step (paper Sec. 2.2 and Sec. 3.1).
+//
+// A cell is (level, i_x, i_y, i_z) on the periodic grid of base[d] * 3^level
+// cells per axis.  The tree is the set of leaves plus the set of refined
+// (inner) nodes.  Cells are numbered in depth-first order of the tree (base
+// cells lexicographic with x fastest, children likewise); the skeleton and
+// enclave batches are index lists into that numbering.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace ader {
+
+struct Key {
+  int level;
+  int x[3];
+};
+
+uint64_t pack(const Key& k);
+Key unpack(uint64_t v);
+
+// One transition: the coarse cell's face (dir, coarse_side) is split into
+// 3^(d-1) child faces; child sigma (lowest tangential direction fastest)
+// belongs to fine cell child_fine[parent * 3^(d-1) + sigma].
+struct ParentFace {
+  int32_t coarse;
+  int32_t dir;
+  int32_t coarse_side;  // 0: the coarse cell's -dir face, 1: its +dir face
+  int32_t pad;
+};
+
+struct ConfFace {
+  int32_t left;   // cell whose +dir face this is
+  int32_t right;  // cell whose -dir face this is
+  int32_t dir;
+  int32_t pad;
+};
+
+// How a cell of the new mesh gets its data during a remesh.
+struct TransferItem {
+  int32_t kind;   // 0 copy, 1 interpolate from parent, 2 project from children
+  int32_t src;    // old cell index (kinds 0, 1) or offset into child list (kind 2)
+  int32_t child;  // kind 1: child position s_x + 3 s_y + 9 s_z inside the parent
+  int32_t pad;
+};
+
+class Tree {
+ public:
+  Tree() = default;
+  Tree(int dim, const int base[3], int max_level);
+
+  int dim() const { return dim_; }
+  int max_level() const { return max_level_; }
+  int64_t dims(int level, int d) const;
+
+  // The ordered cell list and its derived structures.  Rebuilt by build().
+  std::vector<Key> cells;
+  std::vector<uint8_t> transition;        // per cell: touches a resolution transition
+  std::vector<ConfFace> conf_all;         // conforming faces, build order
+  std::vector<ParentFace> parents;
+  std::vector<int32_t> child_fine;
+
+  // Skeleton/enclave split (classify()): skeleton = transition cells plus
+  // cells flagged for refinement.  conf is conf_all with the faces whose two
+  // cells are both skeleton first (n_conf_skeleton of them).
+  std::vector<uint8_t> skeleton;
+  std::vector<int32_t> skel_cells, encl_cells;
+  std::vector<ConfFace> conf;
+  int64_t n_conf_skeleton = 0;
+
+  // Rebuild order and faces.  Returns false and sets error() if the mesh is
+  // not 2:1 balanced.  Leaves the split as transition cells only.
+  bool build();
+  // Recompute the split; refine_flags (per cell, may be null) adds cells with
+  // a positive flag to the skeleton.
+  void classify(const int8_t* refine_flags);
+
+  // Apply per-cell flags (+1 refine, -1 coarsen, 0 keep) in the order of
+  // `cells`.  Fills the transfer plan for the new order (and the child list
+  // for projections).  Calls build() on the new mesh.
+  bool remesh(const int8_t* flags, std::vector<TransferItem>* plan,
+              std::vector<int32_t>* coarsen_children);
+
+  // Geometric criterion around a ball (periodic distance): refine leaves
+  // below max_level whose box meets the ball, coarsen leaves above level 0
+  // whose parent's box misses it.
+  void sphere_flags(const double center[3], double radius, const double lo[3],
+                    const double hi[3], int8_t* flags) const;
+
+  const std::string& error() const { return error_; }
+
+ private:
+  bool is_leaf(const Key& k) const { return leaves_.count(pack(k)) != 0; }
+  bool is_refined(const Key& k) const { return refined_.count(pack(k)) != 0; }
+  Key neighbor(const Key& k, int dir, int side) const;
+  Key parent(const Key& k) const;
+  Key child(const Key& k, const int s[3]) const;
+  void touching_children(const Key& k, int dir, int side, std::vector<Key>* out) const;
+  int max_level_across(const Key& k, int dir, int side) const;
+  int max_level_below_face(const Key& k, int dir, int side) const;
+  void split(const Key& k);
+  void rebuild_refined();
+  void order_cells(std::vector<Key>* out) const;
+  void dfs(const Key& k, std::vector<Key>* out) const;
+
+  int dim_ = 0;
+  int base_[3] = {1, 1, 1};
+  int max_level_ = 0;
+  std::unordered_set<uint64_t> leaves_;
+  std::unordered_set<uint64_t> refined_;
+  std::string error_;
+};
+
+}  // namespace ader

@@ -1,0 +1,247 @@
+// Space-time predictor C_STP (paper Sec. 2.1, Eq. (3), Algorithm 1 first
+// loop) fused with id|T+dT, id|dc and the corrector's volume term.
+//
+// Per cell and spatial node i, Picard iteration on the time-weak predictor
+// equation (integrated by parts in time with the upwind inflow u, strong-form
+// nodal flux divergence, neighbours ignored):
+//   q^(0)_k   = u
+//   q^(r+1)_k = u - dt sum_l Mt[k][l] sum_d h_d^-1 (D^(d) f_d(q^(r)_l))_i,
+// with Mt = K1^{-1} diag(w) (K1^{-1} theta(0) = 1 folds the inflow term).
+// After I iterations:
+//   Q-bar   = sum_k w_k q_k,  F-bar_d = sum_k w_k f_d(q_k)
+//   u*      = u + dt sum_d h_d^-1 (V^(d) F-bar_d)_i,  V = W^-1 D^T W
+//   faces   : Q-bar and F-bar_d extrapolated with phi(0), phi(1) along d.
+//
+// GB300 mapping: one thread per spatial node, CPB cells per CTA.  Each thread
+// keeps its node's space-time column q[n][m] and the Picard accumulator in
+// registers; the fluxes of one time slice are staged in shared memory so that
+// the 1D derivative contractions along every axis read neighbours on chip.
+// The space-time block never touches HBM: the kernel reads u once and writes
+// u* and the 2d face blocks once.
+#pragma once
+#include "kernels.h"
+#include "pde.cuh"
+
+namespace ader {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int DIM, int N>
+struct PredictShape {
+  static constexpr int n = N + 1;
+  static constexpr int NS = ipow(n, DIM);
+  static constexpr int NF = ipow(n, DIM - 1);
+  static constexpr int CPB = NS >= 128 ? 1 : (256 / NS);
+  static constexpr int THREADS = CPB * NS;
+};
+
+template <int DIM, int N, class PDE, class Real>
+__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
+    predict_kernel(const PredictArgs a) {
+  using S = PredictShape<DIM, N>;
+  constexpr int n = S::n, NS = S::NS, NF = S::NF, CPB = S::CPB, M = PDE::M;
+  __shared__ Real sD[n * n], sMt[n * n], sV[n * n], sw[n], sp0[n], sp1[n];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // fb[CPB][DIM][M][NS] fluxes of one slice (later F-bar); qs[CPB][M][NS] Q-bar
+  Real* fb = reinterpret_cast<Real*>(smem_raw);
+  Real* qs = fb + CPB * DIM * M * NS;
+
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += blockDim.x) {
+    sD[t] = Real(a.B.D[t / n][t % n]);
+    sMt[t] = Real(a.B.Mt[t / n][t % n]);
+    sV[t] = Real(a.B.V[t / n][t % n]);
+  }
+  if (tid < n) {
+    sw[tid] = Real(a.B.w[tid]);
+    sp0[tid] = Real(a.B.phi0[tid]);
+    sp1[tid] = Real(a.B.phi1[tid]);
+  }
+
+  const int cl = tid / NS;
+  const int node = tid - cl * NS;
+  const int64_t slot = int64_t(blockIdx.x) * CPB + cl;
+  const bool valid = slot < a.count;
+  const int64_t cell = valid ? int64_t(a.cells[slot]) : 0;
+
+  int id[3] = {node % n, (node / n) % n, node / (n * n)};
+  const int stride[3] = {1, n, n * n};
+  Real ih[DIM];
+  double ihd[DIM];
+  {
+    const int lv = valid ? int(a.level[cell]) : 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      ihd[d] = a.inv_h[lv][d];
+      ih[d] = Real(ihd[d]);
+    }
+  }
+  const double dt = *a.dt;
+  const Real dtR = Real(dt);
+  const Real gamma = Real(a.gamma);
+
+  Real uu[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v)
+    uu[v] = valid ? Real(a.u[(cell * M + v) * NS + node]) : Real(v == 0 ? 1 : 0);
+  if (!valid && PDE::kPositivity) uu[M - 1] = Real(2.5);
+
+  Real q[n][M];
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < M; ++v) q[k][v] = uu[v];
+
+  Real* my_fb = fb + cl * DIM * M * NS;
+  Real* my_qs = qs + cl * M * NS;
+  __syncthreads();
+
+  for (int r = 0; r < a.iters; ++r) {
+    Real acc[n][M];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < M; ++v) acc[k][v] = Real(0);
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      Real f[DIM][M];
+      PDE::fluxes(q[l], f, gamma);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+#pragma unroll
+        for (int v = 0; v < M; ++v) my_fb[(d * M + v) * NS + node] = f[d][v];
+      __syncthreads();
+      Real g[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) g[v] = Real(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const Real* Drow = sD + id[d] * n;
+        const int base = node - id[d] * stride[d];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const Real* line = my_fb + (d * M + v) * NS + base;
+          Real s = Real(0);
+#pragma unroll
+          for (int j = 0; j < n; ++j) s = fma(Drow[j], line[j * stride[d]], s);
+          g[v] = fma(ih[d], s, g[v]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const Real c = sMt[k * n + l];
+#pragma unroll
+        for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < M; ++v) q[k][v] = fma(-dtR, acc[k][v], uu[v]);
+  }
+
+  // Time averages of the final iterate and of its fluxes.
+  Real qb[M], Fb[DIM][M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) qb[v] = Real(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int v = 0; v < M; ++v) Fb[d][v] = Real(0);
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    Real f[DIM][M];
+    PDE::fluxes(q[k], f, gamma);
+    const Real wk = sw[k];
+#pragma unroll
+    for (int v = 0; v < M; ++v) qb[v] = fma(wk, q[k][v], qb[v]);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int v = 0; v < M; ++v) Fb[d][v] = fma(wk, f[d][v], Fb[d][v]);
+  }
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    finite = finite && isfinite(qb[v]);
+    my_qs[v * NS + node] = qb[v];
+  }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      finite = finite && isfinite(Fb[d][v]);
+      my_fb[(d * M + v) * NS + node] = Fb[d][v];
+    }
+  if (valid && !finite) atomicOr(a.status, kStatusNonFinitePredictor);
+  __syncthreads();
+  if (!valid) return;
+
+  // Corrector volume term, contraction in Real, added to u in FP64.
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    double vol = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const Real* Vrow = sV + id[d] * n;
+      const Real* line = my_fb + (d * M + v) * NS + node - id[d] * stride[d];
+      Real s = Real(0);
+#pragma unroll
+      for (int j = 0; j < n; ++j) s = fma(Vrow[j], line[j * stride[d]], s);
+      vol = fma(ihd[d], double(s), vol);
+    }
+    const int64_t gi = (cell * M + v) * NS + node;
+    a.ustar[gi] = fma(dt, vol, a.u[gi]);
+  }
+
+  // id|dc: extrapolate Q-bar and the normal flux F-bar_d to the 2d faces.
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (id[d] != (side == 0 ? 0 : n - 1)) continue;
+      const Real* phi = side == 0 ? sp0 : sp1;
+      int fnode;
+      if (DIM == 2) {
+        fnode = d == 0 ? id[1] : id[0];
+      } else {
+        fnode = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
+      }
+      const int base = node - id[d] * stride[d];
+      const int64_t fo = ((cell * 2 * DIM + 2 * d + side) * M) * NF + fnode;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const Real* lq = my_qs + v * NS + base;
+        const Real* lf = my_fb + (d * M + v) * NS + base;
+        Real sq = Real(0), sf = Real(0);
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          sq = fma(phi[j], lq[j * stride[d]], sq);
+          sf = fma(phi[j], lf[j * stride[d]], sf);
+        }
+        a.faceQ[fo + v * NF] = double(sq);
+        a.faceF[fo + v * NF] = double(sf);
+      }
+    }
+  }
+}
+
+template <int DIM, int N, class PDE, class Real>
+cudaError_t launch_predict_t(const PredictArgs& a, cudaStream_t s) {
+  using S = PredictShape<DIM, N>;
+  if (a.count == 0) return cudaSuccess;
+  const size_t smem = size_t(S::CPB) * (DIM + 1) * PDE::M * S::NS * sizeof(Real);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(predict_kernel<DIM, N, PDE, Real>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t blocks = (a.count + S::CPB - 1) / S::CPB;
+  predict_kernel<DIM, N, PDE, Real><<<dim3(unsigned(blocks)), dim3(S::THREADS), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ader

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on
+identical seeded inputs.  FP64 bar: relative L2 <= 1e-12 per field (the
+spec tolerance); FP32-predictor bar: relative L2 <= 1e-6."""
+import numpy as np
+import pytest
+
+from oracle import ader as oader, basis as obasis, mesh as omesh, pde as opde, step as ostep
+import workloads
+from gpu_helpers import build_pair, lib_keys, rel_l2
+from oracle_helpers import random_state, state_from
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-6
+
+
+def stage_parity(dim, order, pde, base, max_level, centers, radius, seed, tol=TOL64,
+                 precision="fp64"):
+    import paper_1806_07984_gb300.ader as A
+    solver, om, perm = build_pair(dim, order, pde, base, max_level, centers, radius,
+                                  precision=precision)
+    B = obasis.Basis(order)
+    P = opde.make_pde(pde, dim)
+    u0 = random_state(om, B, pde, seed)
+    h = om.cell_widths()
+    dt = oader.cfl_dt(u0, h, P, order, cfl=workloads.ADER_CFL[order])
+    ref = ostep.step(om, u0, dt, P, B)
+    solver.set_state(u0[perm])
+    solver.set_dt(dt)
+    solver.predict()
+    ustar = solver.get_field(A.ADER_FIELD_USTAR).cpu().numpy()
+    fq = solver.get_field(A.ADER_FIELD_FACE_Q).cpu().numpy()
+    ff = solver.get_field(A.ADER_FIELD_FACE_F).cpu().numpy()
+    assert rel_l2(ustar - u0[perm], ref.ustar[perm] - u0[perm]) < max(tol * 1e3, 1e-9)
+    assert rel_l2(ustar, ref.ustar[perm]) < tol
+    assert rel_l2(fq, ref.Qf[perm]) < tol
+    assert rel_l2(ff, ref.Ff[perm]) < tol
+    solver.riemann()
+    fs = solver.get_field(A.ADER_FIELD_FSTAR).cpu().numpy()
+    assert rel_l2(fs, ref.Fs[perm]) < tol
+    dt_next = solver.dt.clone()
+    solver.correct(dt_next)
+    u1 = solver.get_state().cpu().numpy()
+    assert rel_l2(u1 - u0[perm], ref.u[perm] - u0[perm]) < max(tol * 1e3, 1e-9)
+    assert rel_l2(u1, ref.u[perm]) < tol
+    assert abs(dt_next.item() - ref.dt_next) < tol * ref.dt_next
+    assert solver.status() == 0
+    n = solver.mesh_info()
+    solver.close()
+    return n
+
+
+@pytest.mark.parametrize("order", [1, 3, 5, 7])
+def test_uniform_2d_euler_stages(order):
+    # 7 x 7 = 49 cells: not a multiple of the cells per CTA (ragged tail)
+    n = stage_parity(2, order, "euler", 7, 0, (), 0.1, seed=order)
+    assert n[3] == 0
+
+
+@pytest.mark.parametrize("order", [2, 3, 5])
+def test_amr_2d_euler_stages(order):
+    n = stage_parity(2, order, "euler", 9, 2, [(0.45, 0.55)] * 2, 0.15, seed=10 + order)
+    assert n[3] > 0 and n[1] > 0
+
+
+@pytest.mark.parametrize("order", [2, 3, 5])
+def test_amr_3d_euler_stages(order):
+    n = stage_parity(3, order, "euler", 3, 2, [(0.45, 0.5, 0.55)] * 2, 0.12, seed=20 + order)
+    assert n[3] > 0
+
+
+@pytest.mark.parametrize("dim,order", [(2, 4), (3, 4)])
+def test_amr_acoustics_stages(dim, order):
+    c = (0.45, 0.5, 0.55)[:dim]
+    stage_parity(dim, order, "acoustics", 3 if dim == 3 else 9, 2, [c] * 2, 0.12, seed=30 + dim)
+
+
+@pytest.mark.parametrize("order", [3, 5])
+def test_fp32_predictor_bound(order):
+    stage_parity(3, order, "euler", 3, 1, [(0.5, 0.5, 0.5)], 0.2, seed=40, tol=TOL32,
+                 precision="fp32")
+
+
+def test_single_cell_self_periodic_3d():
+    stage_parity(3, 3, "euler", 1, 0, (), 0.1, seed=50)
+
+
+def test_3d_order7_fp64():
+    stage_parity(3, 7, "euler", 2, 0, (), 0.1, seed=51)
+
+
+def test_streams_step_matches_oracle_sequence():
+    """ader_step on the two prioritised streams, dt kept on the device, three
+    steps, against three oracle steps with the oracle's own dt sequence."""
+    dim, order = 2, 3
+    solver, om, perm = build_pair(dim, order, "euler", 9, 2, [(0.4, 0.6)] * 2, 0.15)
+    B = obasis.Basis(order)
+    P = opde.Euler(dim)
+    u = state_from(om, B, lambda X: workloads.isentropic_vortex(X[0], X[1], center=(0.4, 0.6)))
+    h = om.cell_widths()
+    solver.set_state(u[perm])
+    dt = oader.cfl_dt(u, h, P, order, cfl=workloads.ADER_CFL[order])
+    solver.compute_dt()
+    assert abs(solver.dt.item() - dt) < 1e-13 * dt
+    for _ in range(3):
+        out = ostep.step(om, u, dt, P, B)
+        u, dt = out.u, out.dt_next
+    solver.step(3)
+    got = solver.get_state().cpu().numpy()
+    assert rel_l2(got, u[perm]) < TOL64
+    assert abs(solver.dt.item() - dt) < 1e-12 * dt
+    assert solver.status() == 0
+    assert np.any(solver.skeleton())
+
+
+def test_remesh_transfer_parity():
+    """Refine/coarsen a state-carrying mesh with a moving ball: the library's
+    transferred state equals the oracle's (interpolation, L2 projection)."""
+    dim, order = 3, 3
+    solver, om, perm = build_pair(dim, order, "euler", 3, 2, [(0.5, 0.5, 0.5)] * 2, 0.15)
+    B = obasis.Basis(order)
+    u = state_from(om, B, lambda X: workloads.density_bubble(X, sigma=0.2))
+    solver.set_state(u[perm])
+    changed = 0
+    for c in [(0.6, 0.55, 0.5), (0.8, 0.7, 0.6), (0.1, 0.9, 0.05)]:
+        fl = omesh.sphere_flags(om, c, 0.15)
+        before = len(om.cells)
+        solver.remesh(fl[perm])
+        u = om.remesh(u, fl, B)
+        changed += len(om.cells) != before
+        keys = lib_keys(solver)
+        assert sorted(keys) == om.cells
+        perm = np.array([om.index[k] for k in keys])
+        assert rel_l2(solver.get_state().cpu().numpy(), u[perm]) < 1e-13
+    assert changed >= 2
+
+
+def test_nonphysical_state_sets_status():
+    """A negative density in one cell is reported through the status word
+    (the kernels check the state; nothing faults)."""
+    solver, om, perm = build_pair(2, 2, "euler", 3, 0)
+    B = obasis.Basis(2)
+    u = random_state(om, B, "euler", 1)
+    u[4, 0] = -1.0
+    solver.set_state(u[perm])
+    solver.set_dt(1e-3)
+    solver.step(1)
+    assert solver.status() & 2
+    assert solver.status() == 0   # reading clears it

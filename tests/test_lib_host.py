@@ -1,0 +1,113 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol,
+and its host spacetree logic equals the oracle's (bit-exact integer work)."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mesh as omesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_1806_07984_gb300 import ader, build
+    build.build()
+    ader.lib()
+    return ader
+
+
+def test_exports_match_header(A):
+    header = open(os.path.join(ROOT, "include", "ader.h")).read()
+    declared = set(re.findall(r"\b(ader_\w+)\s*\(", header))
+    declared -= {"ader_ctx", "ader_mesh"}
+    assert declared == set(A.EXPORTS), declared ^ set(A.EXPORTS)
+    L = A.lib()
+    for name in declared:
+        assert hasattr(L, name)
+    assert A.ader_error_string(-4) == "non-physical state"
+
+
+def lib_mesh_state(A, m, dim):
+    cells, skel = A.ader_mesh_leaves(m)
+    keys = [(int(c[0]), tuple(int(x) for x in c[1:1 + dim])) for c in cells]
+    conf, par, kids = A.ader_mesh_faces(m, dim)
+    return keys, skel.astype(bool), conf, par, kids
+
+
+def oracle_face_sets(om):
+    conf, parents = om.faces()
+    cs = set((om.cells[a], om.cells[b], d) for a, b, d in conf)
+    ps = set((om.cells[c], d, s, tuple(om.cells[f] for f, _ in kids)) for c, d, s, kids in parents)
+    return cs, ps
+
+
+def lib_face_sets(keys, conf, par, kids):
+    cs = set((keys[a], keys[b], int(d)) for a, b, d in conf)
+    ps = set((keys[c], int(d), int(s), tuple(keys[f] for f in kids[i])) for i, (c, d, s) in enumerate(par))
+    return cs, ps
+
+
+def drive(A, dim, base, max_level, centers, radius):
+    """Apply the same sphere-flag sequence to both meshes; compare after each."""
+    om = omesh.Mesh(dim, (base,) * dim, max_level)
+    lm = A.ader_mesh_create(dim, (base,) * dim, max_level)
+    try:
+        for center in centers:
+            keys = lib_mesh_state(A, lm, dim)[0]
+            okeys = om.cells
+            assert sorted(keys) == okeys
+            fl_o = omesh.sphere_flags(om, center, radius)
+            fl_l = A.ader_mesh_sphere_flags(lm, center, radius)
+            perm = [om.index[k] for k in keys]
+            assert np.array_equal(fl_l, fl_o[perm])
+            import oracle.basis as ob
+            B = ob.Basis(1)
+            om.remesh(np.zeros((len(om.cells), 1) + (2,) * dim), fl_o, B)
+            A.ader_mesh_adapt(lm, fl_l)
+            keys, skel, conf, par, kids = lib_mesh_state(A, lm, dim)
+            assert sorted(keys) == om.cells
+            oskel = om.skeleton()
+            assert np.array_equal(skel, oskel[[om.index[k] for k in keys]])
+            assert lib_face_sets(keys, conf, par, kids) == oracle_face_sets(om)
+            nconf_sk = sum(1 for a, b, _ in conf if skel[a] and skel[b])
+            assert all(skel[a] and skel[b] for a, b, _ in conf[:nconf_sk])
+        return len(om.cells)
+    finally:
+        A.ader_mesh_destroy(lm)
+
+
+def test_mesh_parity_2d(A):
+    centers = [(0.45, 0.55), (0.45, 0.55), (0.6, 0.65), (0.75, 0.8), (0.95, 0.05)]
+    assert drive(A, 2, 9, 2, centers, 0.15) > 81
+
+
+def test_mesh_parity_3d(A):
+    centers = [(0.5, 0.5, 0.5), (0.5, 0.5, 0.5), (0.62, 0.6, 0.58), (0.9, 0.1, 0.95)]
+    assert drive(A, 3, 3, 2, centers, 0.2) > 27
+
+
+def test_mesh_parity_deep_2d(A):
+    """Three levels with a cascade of balance refinements."""
+    centers = [(0.3, 0.3)] * 3 + [(0.32, 0.31), (0.5, 0.5)]
+    assert drive(A, 2, 3, 3, centers, 0.02) > 9
+
+
+def test_mesh_single_cell(A):
+    lm = A.ader_mesh_create(3, (1, 1, 1), 1)
+    try:
+        C, nskel, nconf, npar = A.ader_mesh_sizes(lm)
+        assert (C, nskel, nconf, npar) == (1, 0, 3, 0)
+        conf, _, _ = A.ader_mesh_faces(lm, 3)
+        assert conf.tolist() == [[0, 0, 0], [0, 0, 1], [0, 0, 2]]
+    finally:
+        A.ader_mesh_destroy(lm)
+
+
+def test_mesh_bad_arguments(A):
+    with pytest.raises(A.AderError):
+        A.ader_mesh_create(4, (3, 3, 3), 1)
+    with pytest.raises(A.AderError):
+        A.ader_mesh_create(2, (0, 3, 1), 1)
