@@ -38,6 +38,8 @@ FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 128 FP32 lanes/SM, FMA = 2 
 WORKLOADS = {
     "euler3d-n5-amr": dict(dim=3, order=5, base=27, max_level=2, radius=0.15, remesh_every=10,
                            init="bubble"),
+    "euler3d-n5-base27": dict(dim=3, order=5, base=27, max_level=0, radius=0.0, remesh_every=0,
+                              init="bubble"),
     "euler3d-n7-amr": dict(dim=3, order=7, base=27, max_level=2, radius=0.15, remesh_every=10,
                            init="bubble"),
     "euler2d-n3-vortex": dict(dim=2, order=3, base=27, max_level=0, radius=0.0, remesh_every=0,
