@@ -183,6 +183,33 @@ ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
 /* Number of kernel launches this context has enqueued so far. */
 ader_status ader_launch_count(ader_ctx* ctx, int64_t* out);
 
+/* ---- Allocation-free time step ------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: code running inside a memory pool or arena
+ * it does not own (a host framework that forbids cudaMalloc once it has
+ * started, or must not fragment its pool), or a path that must not fail for
+ * lack of memory.  It computes the same global time step as ader_compute_dt,
+ *   *dt_dev = cfl / max over cells and nodes of sum_d lambda_d(u) / h_d,
+ * without a context and without allocating: it calls no cudaMalloc, cudaFree
+ * or allocating library routine.  Its scratch (one FP64 partial maximum per
+ * CTA) is a fixed device array inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   u_dev      device state u[c][var][node] (layout as above), ncells cells
+ *   level_dev  device int8 level per cell, 0 <= level < 8 (other values make
+ *              the result NaN); h_d = (hi[d] - lo[d]) / (base[d] 3^level)
+ *   dt_dev     device double receiving dt (NaN if a state is non-physical)
+ * Sizes: 1 <= ncells <= ADER_DT_STATIC_MAX_CELLS, else ADER_ERR_ARG.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites the slots it reads, so calls
+ * that overlap on the GPU (different streams, or several host threads) race:
+ * serialise them. */
+#define ADER_DT_STATIC_MAX_CELLS 1048576
+ader_status ader_compute_dt_static(int dim, int order, ader_pde pde, double gamma, double cfl,
+                                   const int base[3], const double lo[3], const double hi[3],
+                                   int64_t ncells, const double* u_dev, const int8_t* level_dev,
+                                   double* dt_dev, void* stream);
+
 /* ---- Host-only mesh handle (no device needed) ---------------------------
  * The same spacetree logic as the context's mesh (Sec. 2.2 three-partitioning,
  * 2:1 face balance, coarsening rules, skeleton of Sec. 3.1), usable without a

@@ -30,7 +30,8 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_correct", "ader_step", "ader_remesh", "ader_classify", "ader_sphere_flags",
            "ader_status_word", "ader_launch_count", "ader_mesh_create", "ader_mesh_destroy",
            "ader_mesh_adapt", "ader_mesh_sizes", "ader_mesh_leaves", "ader_mesh_faces",
-           "ader_mesh_sphere_flags"]
+           "ader_mesh_sphere_flags", "ader_compute_dt_static"]
+ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
 class AderError(RuntimeError):
@@ -90,6 +91,9 @@ def lib():
         "ader_mesh_leaves": ([_vp, _vp, _vp], ctypes.c_int),
         "ader_mesh_faces": ([_vp, _vp, _vp, _vp], ctypes.c_int),
         "ader_mesh_sphere_flags": ([_vp, _vp, ctypes.c_double, _vp, _vp, _vp], ctypes.c_int),
+        "ader_compute_dt_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
+                                    _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -277,3 +281,17 @@ def ader_mesh_sphere_flags(mesh, center, radius, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.
     _check(None, lib().ader_mesh_sphere_flags(mesh, _ptr(c), float(radius), _ptr(lo_), _ptr(hi_),
                                               _ptr(out)), "ader_mesh_sphere_flags")
     return out
+
+
+def ader_compute_dt_static(dim, order, pde, gamma, cfl, base, lo, hi, ncells, u_dev, level_dev,
+                           dt_dev, stream=None):
+    """Allocation-free global time step (no context); see include/ader.h."""
+    b = np.ones(3, dtype=np.int32)
+    b[:dim] = base[:dim]
+    lo_ = np.zeros(3)
+    lo_[:dim] = lo[:dim]
+    hi_ = np.ones(3)
+    hi_[:dim] = hi[:dim]
+    _check(None, lib().ader_compute_dt_static(dim, order, pde, gamma, cfl, _ptr(b), _ptr(lo_),
+                                              _ptr(hi_), ncells, _ptr(u_dev), _ptr(level_dev),
+                                              _ptr(dt_dev), stream), "ader_compute_dt_static")
