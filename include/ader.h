@@ -6,12 +6,12 @@
  * Methods on Dynamically Adaptive Meshes"):
  *   - the PDE is the first-order balance law of Eq. (1) with S = 0, delta = 0;
  *   - one step is Q(T+dT) = (C_Corr o F_R o id|dc + id|T+dT) o C_STP Q(T),
- *     Eq. (3) and Algorithm 1: a space-time predictor per cell, Riemann solves
+ *     Eq. (4) and Algorithm 1: a space-time predictor per cell, Riemann solves
  *     per face, a corrector per cell;
- *   - at a resolution transition (Sec. 2.2) coarse predictor data are
+ *   - at a resolution transition (Sec. 2.3) coarse predictor data are
  *     interpolated to virtual child faces, Riemann is solved on the child
  *     faces only, and the results are restricted into the parent face;
- *   - dynamic adaptivity (Sec. 2.2) refines/coarsens cells between steps;
+ *   - dynamic adaptivity (Sec. 2.3) refines/coarsens cells between steps;
  *   - enclave tasking (Sec. 3) becomes a skeleton batch (cells at resolution
  *     transitions or flagged for refinement) on a high-priority CUDA stream and
  *     an enclave batch on a low-priority stream.
@@ -133,13 +133,13 @@ ader_status ader_get_field(ader_ctx* ctx, ader_field f, double* out, int on_devi
  * *dt_dev = cfl / max over cells and nodes of sum_d lambda_d(u) / h_d. */
 ader_status ader_compute_dt(ader_ctx* ctx, double* dt_dev, void* stream);
 
-/* C_STP with id|T+dT and id|dc (Eq. (3), Algorithm 1 first loop) on the cells
+/* C_STP with id|T+dT and id|dc (Eq. (4), Algorithm 1 first loop) on the cells
  * of `set`: Picard iterations of the space-time predictor, then the time
  * averages of the predictor and of its fluxes, their extrapolation to the 2d
  * faces (ADER_FIELD_FACE_Q/F) and u* = u + dt * volume term (ADER_FIELD_USTAR). */
 ader_status ader_predict(ader_ctx* ctx, const double* dt_dev, ader_set set, void* stream);
 
-/* F_R (Algorithm 1 second loop) with the AMR tasks of Sec. 2.2.
+/* F_R (Algorithm 1 second loop) with the AMR tasks of Sec. 2.3.
  * ADER_SKELETON: Rusanov on child faces (coarse data interpolated into the
  * virtual cells' faces), restriction into the parent faces, and conforming
  * faces between two skeleton cells.  ADER_ENCLAVE: the other conforming faces.
@@ -159,7 +159,7 @@ ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_de
  * `stream`; later work on `stream` sees the result. */
 ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
 
-/* Dynamic adaptivity (Sec. 2.2): flags per cell in mesh order (+1 refine,
+/* Dynamic adaptivity (Sec. 2.3): flags per cell in mesh order (+1 refine,
  * -1 coarsen, 0 keep).  Refines flagged cells below max_level, restores 2:1
  * face balance by further refinement, coarsens complete families of flagged
  * leaves whose parent stays balanced, and transfers the state (interpolation
@@ -211,8 +211,8 @@ ader_status ader_compute_dt_static(int dim, int order, ader_pde pde, double gamm
                                    double* dt_dev, void* stream);
 
 /* ---- Host-only mesh handle (no device needed) ---------------------------
- * The same spacetree logic as the context's mesh (Sec. 2.2 three-partitioning,
- * 2:1 face balance, coarsening rules, skeleton of Sec. 3.1), usable without a
+ * The same spacetree logic as the context's mesh (Sec. 2.3 three-partitioning,
+ * 2:1 face balance, coarsening rules, skeleton of Sec. 3), usable without a
  * GPU for planning and inspection. */
 typedef struct ader_mesh ader_mesh;
 

@@ -1,6 +1,6 @@
 """Cell and face tasks of one ADER-DG step (oracle; test infrastructure).
 
-Sec. 2.1-2.2 and Eq. (3) of the paper split one step into the space-time
+Sec. 2.1-2.2 and Eq. (4) of the paper split one step into the space-time
 predictor C_STP with its projections id|dc (onto the 2d faces) and id|T+dT,
 the Riemann solves F_R over the faces, and the corrector C_Corr.  The paper
 defers the formulas to the ADER-DG literature; this module writes them out for
@@ -76,7 +76,7 @@ def picard_predictor(u, h, dt, pde, B, iters):
 
 
 def ck_predictor(u, h, dt, pde, B):
-    """Cauchy-Kowalevski predictor for a linear PDE (Sec. 2.3).
+    """Cauchy-Kowalevski predictor for a linear PDE (Sec. 2.4).
 
     Time derivatives by the PDE itself: d_t^0 u = u and
     d_t^{k+1} u = -sum_d h_d^-1 D^(d) f_d(d_t^k u) (f linear).  The space-time
@@ -150,7 +150,7 @@ def project_to_faces(qbar, fbar, B):
 def rusanov(QL, FL, QR, FR, pde, dr):
     """Rusanov flux F* = (F_L + F_R)/2 - s (Q_R - Q_L)/2 on faces [f, var, node].
 
-    s is one estimate of the largest eigenvalue per face (Sec. 2.3): the
+    s is one estimate of the largest eigenvalue per face (Sec. 2.4): the
     maximum of lambda_dr over the face nodes of both sides.
     """
     lamL = pde.max_speed(np.moveaxis(QL, 1, 0), dr)

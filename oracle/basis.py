@@ -15,7 +15,7 @@ one-dimensional ingredients of that ansatz from their definitions:
 * ``prolongation``      - P_s with (P_s)_ij = phi_j((s + xi_i) / 3), s = 0, 1, 2:
                           interpolation into the three children of 3-partitioning;
 * ``restriction``       - R_s = (1/3) W^-1 P_s^T W, the mass-weighted transpose of
-                          P_s (the "transpose of the interpolation" of Sec. 2.2,
+                          P_s (the "transpose of the interpolation" of Sec. 2.3,
                           read as the L2 projection so that it conserves).
 
 All arithmetic is float64.

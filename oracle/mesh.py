@@ -1,13 +1,13 @@
 """Adaptive 3^d spacetree mesh (oracle; test infrastructure).
 
-Sec. 2.2 of the paper: a conformal base grid at level l_min, every refined cell
+Sec. 2.3 of the paper: a conformal base grid at level l_min, every refined cell
 split into 3^d children (three-partitioning), the unrefined cells forming the
 adaptive mesh.  Here a cell is the key (level, (i_x, i_y[, i_z])) with integer
 coordinates in the grid of ``base * 3**level`` cells per axis; the domain is a
 periodic box.  The tree is held as a set of leaves; a node is refined when it
 has a leaf below it.
 
-Faces (Sec. 2.2):
+Faces (Sec. 2.3):
 
 * a conforming face joins two leaves of one level;
 * at a resolution transition the coarse cell's face is a parent face, split
@@ -20,7 +20,7 @@ Child faces of a parent are enumerated in lexicographic order of the
 sub-face index s (lowest tangential direction fastest); restriction sums them
 in that order.
 
-Remeshing (Sec. 2.2, the AMR epilogue of the corrector) takes one flag per
+Remeshing (Sec. 2.3, the AMR epilogue of the corrector) takes one flag per
 leaf (+1 refine, -1 coarsen, 0 keep) and applies, in this order:
   1. refine every flagged leaf below ``max_level``;
   2. 2:1 balance: refine any leaf with a face neighbour two or more levels
@@ -196,7 +196,7 @@ class Mesh:
 
     def skeleton(self, refine_flags=None):
         """Boolean per cell: adjacent to a resolution transition (either side)
-        or flagged for refinement (Sec. 3.1, skeleton cells)."""
+        or flagged for refinement (Sec. 3 and 3.1, skeleton cells)."""
         skel = np.zeros(len(self.cells), dtype=bool)
         _, parents = self.faces()
         for c, _, _, kids in parents:

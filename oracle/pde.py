@@ -3,12 +3,12 @@
 Sources S and point sources delta of Eq. (1) vanish in every workload here.
 Arrays carry the m variables on axis 0: ``q[var, ...]``.
 
-* ``Euler``     - compressible Euler (the paper's Euler application, Sec. 5):
+* ``Euler``     - compressible Euler (the paper's Euler application, Sec. 6):
                   q = (rho, rho v_1..rho v_d, E), p = (gamma-1)(E - |rho v|^2/(2 rho)),
                   f_d = (rho v_d, rho v v_d + p e_d, v_d (E + p)),
                   lambda_d = |v_d| + sqrt(gamma p / rho).
 * ``Acoustics`` - linear acoustics with c = rho = 1 (a linear PDE, for which
-                  Sec. 2.3 names Cauchy-Kowalevski): q = (p, v_1..v_d),
+                  Sec. 2.4 names Cauchy-Kowalevski): q = (p, v_1..v_d),
                   f_d = (v_d, p e_d), lambda_d = 1.
 """
 import numpy as np

@@ -2,7 +2,7 @@
 
 Algorithm 1 of the paper (three task loops: predictor over all cells, Riemann
 over all faces, corrector over all cells), extended by the two AMR tasks of
-Sec. 2.2: interpolation of the coarse predictor into virtual cells ahead of
+Sec. 2.3: interpolation of the coarse predictor into virtual cells ahead of
 the Riemann solves on child faces, and restriction (accumulate-Riemann) of
 the child results into the parent face ahead of the coarse corrector.
 """

@@ -1,5 +1,5 @@
-// Face and cell kernels after the predictor (paper Eq. (3), Algorithm 1
-// second and third loops, Sec. 2.2 interpolation/restriction):
+// Face and cell kernels after the predictor (paper Eq. (4), Algorithm 1
+// second and third loops, Sec. 2.3 interpolation/restriction):
 //
 // * riemann_conf  - F_R on conforming faces: Rusanov on time-averaged face
 //                   data, F* = (F_L + F_R)/2 - s (Q_R - Q_L)/2, one speed s per

@@ -1,6 +1,6 @@
-// Host-side 3^d spacetree (paper Sec. 2.2: three-partitioning on a conformal
+// Host-side 3^d spacetree (paper Sec. 2.3: three-partitioning on a conformal
 // base grid; virtual cells and parent/child faces at resolution transitions;
-// Sec. 3.1: skeleton cells adjacent to a resolution transition).
+// Sec. 3 and 3.1: skeleton cells adjacent to a resolution transition).
 #include "mesh.h"
 
 #include <algorithm>

@@ -1,5 +1,5 @@
 // Host-side 3^d spacetree: leaves, face lists, skeleton/enclave split and
-// remeshing plans for the ADER-DG step (paper Sec. 2.2 and Sec. 3.1).
+// remeshing plans for the ADER-DG step (paper Sec. 2.3 and Sec. 3).
 //
 // A cell is (level, i_x, i_y, i_z) on the periodic grid of base[d] * 3^level
 // cells per axis.  The tree is the set of leaves plus the set of refined

@@ -1,4 +1,4 @@
-// Space-time predictor C_STP (paper Sec. 2.1, Eq. (3), Algorithm 1 first
+// Space-time predictor C_STP (paper Sec. 2.1-2.2, Eq. (4), Algorithm 1 first
 // loop) fused with id|T+dT, id|dc and the corrector's volume term.
 //
 // Per cell and spatial node i, Picard iteration on the time-weak predictor

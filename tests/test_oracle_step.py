@@ -1,5 +1,5 @@
 """Pins of the oracle's full step: free stream, conservation, the operator
-form of Eq. (3), entropy-wave invariants and the design order."""
+form of Eq. (4), entropy-wave invariants and the design order."""
 import numpy as np
 import pytest
 
@@ -52,8 +52,8 @@ def test_conservation_on_amr(which, N, pde_name, request):
 
 
 @pytest.mark.parametrize("which,N", [("amr2d", 3), ("amr3d", 3)])
-def test_operator_form_of_eq3(which, N, request):
-    """Eq. (3) writes the step as Q(T+dT) = C_Corr F_R id|dc Q* + id|T+dT Q*.
+def test_operator_form_of_eq4(which, N, request):
+    """Eq. (4) writes the step as Q(T+dT) = C_Corr F_R id|dc Q* + id|T+dT Q*.
     With q(1) = id|T+dT Q* (the predictor at tau = 1) and the interior
     face traces of F-bar, the corrector is q(1) minus the jump terms
     dt h^-1 w^-1 [phi(1) (F*_+ - F-bar_+) - phi(0) (F*_- - F-bar_-)].
