@@ -50,18 +50,20 @@ WORKLOADS = {
 def predictor_flops_per_cell(dim, order, iters, m):
     """Algorithmic flops of the fused predictor per cell (FMA = 2).
 
-    c_f = 29 flops per Euler flux evaluation (all dim directions, 3D) scaled
-    by dimension; first Picard iteration needs one time slice (constant
-    initial guess); each later iteration n slices of flux, divergence
-    (dim m dot products of length n plus scaling) and time mixing (n m FMAs);
-    then time averages, the volume term and face extrapolation."""
+    c_f: one Euler flux evaluation in all dim directions (reciprocal, dim
+    velocities, kinetic energy, pressure, E + p, dim(dim+1)/2 momentum
+    products, dim pressure terms, dim energy fluxes).  Per node: the first
+    Picard iteration needs one time slice (its guess is constant in time);
+    each later iteration n slices of flux, divergence (dim m dot products of
+    length n) and time mixing (n m FMAs); then n flux evaluations with the
+    time averages, the volume term, and the face extrapolation per face node."""
     n = order + 1
     NS = n ** dim
     NF = n ** (dim - 1)
-    c_f = 1 + dim + 2 * dim + 3 + 1 + dim * (dim + 2)
-    slice_cost = c_f + dim * m * (2 * n + 2) + 2 * n * m
+    c_f = 1 + dim + 2 * dim + 3 + 1 + dim * (dim + 1) // 2 + dim + dim
+    slice_cost = c_f + dim * m * 2 * n + 2 * n * m
     per_node = slice_cost + (iters - 1) * n * slice_cost
-    per_node += n * (c_f + 2 * m * (1 + dim)) + dim * m * (2 * n + 2)
+    per_node += n * (c_f + 2 * m * (1 + dim)) + dim * m * 2 * n + 2 * m
     return NS * per_node + 2 * dim * NF * 2 * m * 2 * n
 
 
@@ -172,6 +174,33 @@ def run_steps(s, wl, k, t_dev, step_base):
     return dofs
 
 
+def l2_error_vs_exact(s, u_dev, t):
+    """Per-variable L2 error (GL quadrature) of the state against the exact
+    translated bubble at time t, relative to the L2 norm of the exact state."""
+    import torch
+    X = s.node_coords()
+    ex = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X, t=t), 0, 1))
+    del X
+    xi = s.nodes()
+    w = np.polynomial.legendre.leggauss(s.n)[1] / 2.0
+    cells = s.cells()
+    vol = np.ones(len(cells))
+    for d in range(s.dim):
+        vol *= (s.cfg.hi[d] - s.cfg.lo[d]) / (s.cfg.base[d] * 3.0 ** cells[:, 0])
+    W = w
+    for _ in range(s.dim - 1):
+        W = np.multiply.outer(W, w)
+    errs, norms = [], []
+    got = u_dev.cpu().numpy()
+    for v in range(s.nvar):
+        e = ((got[:, v] - ex[:, v]) ** 2 * W).reshape(len(cells), -1).sum(axis=1)
+        nrm = (ex[:, v] ** 2 * W).reshape(len(cells), -1).sum(axis=1)
+        errs.append(float(np.sqrt((e * vol).sum())))
+        norms.append(float(np.sqrt((nrm * vol).sum())))
+    del xi
+    return [e / nv for e, nv in zip(errs, norms)], got
+
+
 def time_predictor(s, torch, reps=3):
     """Average duration of one ader_predict(ADER_ALL) launch, CUDA events on
     the launching stream."""
@@ -270,6 +299,7 @@ def main():
     ap.add_argument("--workload", default="euler3d-n5-amr", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -335,13 +365,56 @@ def main():
                 "launch_ms": t_pred * 1e3, "algorithmic_flops": flops,
                 "algorithmic_bytes": bytes_, "hbm_gbs": bytes_ / t_pred / 1e9}
 
+    # ---- mixed precision: FP32 predictor on the same workload -------------------
+    mixed = None
+    if args.precision == "fp64" and not args.no_mixed:
+        t_fp64 = float(t_dev.item())
+        err64, state64 = l2_error_vs_exact(s, s.get_state(), t_fp64)
+        cells64 = s.cells()
+        s.close()
+        del u_dev
+        sm_, u0m = build_problem(wl, "fp32", device)
+        sm_.set_state(torch.from_numpy(u0m).to(device))
+        del u0m
+        sm_.compute_dt()
+        t_m = torch.zeros(1, dtype=torch.float64, device=device)
+        run_steps(sm_, wl, args.warmup, t_m, 0)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        dofs_m = run_steps(sm_, wl, args.steps, t_m, args.warmup)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        el_m = f0.elapsed_time(f1) / 1e3
+        err32, state32 = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()))
+        same_mesh = np.array_equal(sm_.cells(), cells64)
+        t_pred32 = time_predictor(sm_, torch)
+        flops32 = predictor_flops_per_cell(sm_.dim, sm_.order, sm_.order + 1, sm_.nvar) * sm_.ncells
+        mixed = {"precision": "fp32 predictor contractions, fp64 state/faces/corrector",
+                 "value": dofs_m / el_m, "unit": "DoF-updates/s",
+                 "ms_per_step": el_m / args.steps * 1e3,
+                 "speedup_vs_fp64": (dofs_m / el_m) / value,
+                 "l2_rel_err_vs_exact": {"fp64": err64, "fp32": err32,
+                                         "vars": ["rho", "rho_u", "rho_v", "rho_w", "E"][:sm_.nvar]},
+                 "rel_l2_fp32_vs_fp64": (float(np.linalg.norm(state32 - state64) /
+                                               np.linalg.norm(state64)) if same_mesh else None),
+                 "max_abs_fp32_vs_fp64": (float(np.abs(state32 - state64).max())
+                                          if same_mesh else None),
+                 "predictor_launch_ms": t_pred32 * 1e3,
+                 "predictor_tflops": flops32 / t_pred32 / 1e12,
+                 "predictor_frac_of_fp32_peak": flops32 / t_pred32 / 1e12 / FP32_PEAK_TFLOPS}
+        del state64, state32
+        sm_.close()
+    else:
+        s.close()
+        del u_dev
+
     # ---- end to end through the public API with host buffers ---------------
     # Every step: H2D of the state from pinned host memory, one step, D2H of
     # the new state into pinned host memory (the step's result).
     from paper_1806_07984_gb300 import ader as A
     e2e_steps = max(2, min(args.steps, 5))
-    s.close()
-    del u_dev
     s2, u02 = build_problem(wl, args.precision, device)
     host = torch.from_numpy(u02).pin_memory()
     del u02
@@ -383,7 +456,7 @@ def main():
                        "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
                        "remesh_every": wl["remesh_every"]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
-            "clocks": clk}
+            "clocks": clk, "mixed": mixed}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
     if rank == 0:

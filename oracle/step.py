@@ -86,3 +86,80 @@ def step(mesh, u, dt, pde, B, iters=None):
     Fs = riemann(mesh, Qf, Ff, pde, B)
     unew, dt_next = correct(ustar, Fs, h, dt, pde, B)
     return StepOutput(unew, ustar, Qf, Ff, Fs, dt_next)
+
+
+def step_sample(mesh, u, dt, pde, B, targets, iters=None):
+    """u(T + dt) of one full step for the cells ``targets`` only.
+
+    The same tasks as ``step`` evaluated cell by cell: the predictor on the
+    targets and on every cell that shares a face with them (conforming
+    neighbours, finer cells across a parent face, the coarser cell across a
+    child face), the Riemann solves on the targets' faces (prolongation to the
+    virtual face, and restriction of all child faces of a target's parent
+    face), and the corrector on the targets.  Returns (len(targets), m, *nodes).
+    """
+    if iters is None:
+        iters = B.order + 1
+    dim = mesh.dim
+    need = set(int(t) for t in targets)
+    plan = []          # per target: list of (dr, side, kind, data)
+    for t in targets:
+        key = mesh.cells[int(t)]
+        faces = []
+        for dr in range(dim):
+            for side in range(2):
+                nb = mesh.neighbor(key, dr, side)
+                if nb in mesh.leaves:
+                    j = mesh.index[nb]
+                    need.add(j)
+                    faces.append((dr, side, "conf", j))
+                elif nb in mesh.refined:
+                    kids = mesh.touching_children(nb, dr, 1 - side)
+                    idx = [(mesh.index[ck], s) for ck, s in kids]
+                    need.update(j for j, _ in idx)
+                    faces.append((dr, side, "parent", idx))
+                else:
+                    coarse = nb
+                    while coarse not in mesh.leaves:
+                        coarse = (coarse[0] - 1, tuple(c // 3 for c in coarse[1]))
+                    j = mesh.index[coarse]
+                    need.add(j)
+                    s = tuple(key[1][a] - 3 * coarse[1][a] for a in range(dim) if a != dr)
+                    faces.append((dr, side, "child", (j, s)))
+        plan.append(faces)
+    sub = sorted(need)
+    pos = {c: i for i, c in enumerate(sub)}
+    h_all = mesh.cell_widths()
+    ustar, Qf, Ff = predict(u[sub], h_all[sub], dt, pde, B, iters)
+
+    def rus(dr, L, R):
+        (QL, FL), (QR, FR) = L, R
+        return ader.rusanov(QL[None], FL[None], QR[None], FR[None], pde, dr)[0]
+
+    out = []
+    for t, faces in zip(targets, plan):
+        i = pos[int(t)]
+        Fs = np.zeros((1,) + Qf.shape[1:])
+        for dr, side, kind, data in faces:
+            mine = (Qf[i, dr, side], Ff[i, dr, side])
+            if kind == "conf":
+                j = pos[data]
+                other = (Qf[j, dr, 1 - side], Ff[j, dr, 1 - side])
+                Fs[0, dr, side] = rus(dr, mine, other) if side == 1 else rus(dr, other, mine)
+            elif kind == "parent":
+                acc = np.zeros(Qf.shape[3:])
+                for j, s in data:
+                    fine = (Qf[pos[j], dr, 1 - side], Ff[pos[j], dr, 1 - side])
+                    virt = (ader.prolong_face(mine[0], s, B, dim), ader.prolong_face(mine[1], s, B, dim))
+                    F = rus(dr, virt, fine) if side == 1 else rus(dr, fine, virt)
+                    acc += ader.restrict_face(F[None], s, B, dim)[0]
+                Fs[0, dr, side] = acc
+            else:
+                j, s = data
+                jj = pos[j]
+                cq, cf = Qf[jj, dr, 1 - side], Ff[jj, dr, 1 - side]
+                virt = (ader.prolong_face(cq, s, B, dim), ader.prolong_face(cf, s, B, dim))
+                Fs[0, dr, side] = rus(dr, mine, virt) if side == 1 else rus(dr, virt, mine)
+        unew = ader.face_lifting(ustar[i:i + 1], Fs, h_all[[int(t)]], dt, B)
+        out.append(unew[0])
+    return np.stack(out)

@@ -29,12 +29,16 @@ struct Euler {
     }
     const R p = (gamma - R(1)) * fma(R(-0.5), ke, q[DIM + 1]);
     const R Ep = q[DIM + 1] + p;
+    // momentum flux rho v_a v_d is symmetric in (a, d): one product per pair
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       f[d][0] = q[1 + d];
+      f[d][1 + d] = fma(q[1 + d], v[d], p);
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) f[d][1 + a] = q[1 + a] * v[d];
-      f[d][1 + d] += p;
+      for (int a = d + 1; a < DIM; ++a) {
+        f[d][1 + a] = q[1 + a] * v[d];
+        f[a][1 + d] = f[d][1 + a];
+      }
       f[d][DIM + 1] = v[d] * Ep;
     }
   }

@@ -40,19 +40,23 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
     predict_kernel(const PredictArgs a) {
   using S = PredictShape<DIM, N>;
   constexpr int n = S::n, NS = S::NS, NF = S::NF, CPB = S::CPB, M = PDE::M;
-  __shared__ Real sD[n * n], sMt[n * n], sV[n * n], sw[n], sp0[n], sp1[n];
+  // sDh[c][d]: D scaled by 1/h_d of cell c; sMd = -dt Mt; sRs[k] = sum_l sMd[k][l]
+  __shared__ Real sDh[CPB][DIM][n * n], sMd[n * n], sRs[n], sV[n * n], sw[n], sp0[n], sp1[n];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // fb[CPB][DIM][M][NS] fluxes of one slice (later F-bar); qs[CPB][M][NS] Q-bar
   Real* fb = reinterpret_cast<Real*>(smem_raw);
   Real* qs = fb + CPB * DIM * M * NS;
 
   const int tid = threadIdx.x;
+  const double dt = *a.dt;
   for (int t = tid; t < n * n; t += blockDim.x) {
-    sD[t] = Real(a.B.D[t / n][t % n]);
-    sMt[t] = Real(a.B.Mt[t / n][t % n]);
+    sMd[t] = Real(-dt * a.B.Mt[t / n][t % n]);
     sV[t] = Real(a.B.V[t / n][t % n]);
   }
   if (tid < n) {
+    double r = 0.0;
+    for (int l = 0; l < n; ++l) r += a.B.Mt[tid][l];
+    sRs[tid] = Real(-dt * r);
     sw[tid] = Real(a.B.w[tid]);
     sp0[tid] = Real(a.B.phi0[tid]);
     sp1[tid] = Real(a.B.phi1[tid]);
@@ -66,18 +70,16 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
 
   int id[3] = {node % n, (node / n) % n, node / (n * n)};
   const int stride[3] = {1, n, n * n};
-  Real ih[DIM];
   double ihd[DIM];
   {
     const int lv = valid ? int(a.level[cell]) : 0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      ihd[d] = a.inv_h[lv][d];
-      ih[d] = Real(ihd[d]);
-    }
+    for (int d = 0; d < DIM; ++d) ihd[d] = a.inv_h[lv][d];
   }
-  const double dt = *a.dt;
-  const Real dtR = Real(dt);
+  if (node < n * n) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) sDh[cl][d][node] = Real(a.B.D[node / n][node % n] * ihd[d]);
+  }
   const Real gamma = Real(a.gamma);
 
   Real uu[M];
@@ -86,51 +88,58 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
     uu[v] = valid ? Real(a.u[(cell * M + v) * NS + node]) : Real(v == 0 ? 1 : 0);
   if (!valid && PDE::kPositivity) uu[M - 1] = Real(2.5);
 
-  Real q[n][M];
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int v = 0; v < M; ++v) q[k][v] = uu[v];
-
   Real* my_fb = fb + cl * DIM * M * NS;
   Real* my_qs = qs + cl * M * NS;
-  __syncthreads();
 
-  for (int r = 0; r < a.iters; ++r) {
+  // g = sum_d (D/h_d)^(d) f_d(x) at this node, for the slice held in x.
+  auto divergence = [&](const Real(&x)[M], Real(&g)[M]) {
+    Real f[DIM][M];
+    PDE::fluxes(x, f, gamma);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int v = 0; v < M; ++v) my_fb[(d * M + v) * NS + node] = f[d][v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < M; ++v) g[v] = Real(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const Real* Drow = &sDh[cl][d][id[d] * n];
+      const int base = node - id[d] * stride[d];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const Real* line = my_fb + (d * M + v) * NS + base;
+#pragma unroll
+        for (int j = 0; j < n; ++j) g[v] = fma(Drow[j], line[j * stride[d]], g[v]);
+      }
+    }
+    __syncthreads();
+  };
+
+  // First Picard iteration: the initial guess u is constant in time, so one
+  // slice gives every time node: q_k = u - dt (sum_l Mt[k][l]) g(u).
+  Real q[n][M];
+  {
+    Real g[M];
+    divergence(uu, g);
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < M; ++v) q[k][v] = fma(sRs[k], g[v], uu[v]);
+  }
+  for (int r = 1; r < a.iters; ++r) {
     Real acc[n][M];
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int v = 0; v < M; ++v) acc[k][v] = Real(0);
+      for (int v = 0; v < M; ++v) acc[k][v] = uu[v];
 #pragma unroll
     for (int l = 0; l < n; ++l) {
-      Real f[DIM][M];
-      PDE::fluxes(q[l], f, gamma);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d)
-#pragma unroll
-        for (int v = 0; v < M; ++v) my_fb[(d * M + v) * NS + node] = f[d][v];
-      __syncthreads();
       Real g[M];
-#pragma unroll
-      for (int v = 0; v < M; ++v) g[v] = Real(0);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const Real* Drow = sD + id[d] * n;
-        const int base = node - id[d] * stride[d];
-#pragma unroll
-        for (int v = 0; v < M; ++v) {
-          const Real* line = my_fb + (d * M + v) * NS + base;
-          Real s = Real(0);
-#pragma unroll
-          for (int j = 0; j < n; ++j) s = fma(Drow[j], line[j * stride[d]], s);
-          g[v] = fma(ih[d], s, g[v]);
-        }
-      }
-      __syncthreads();
+      divergence(q[l], g);
 #pragma unroll
       for (int k = 0; k < n; ++k) {
-        const Real c = sMt[k * n + l];
+        const Real c = sMd[k * n + l];
 #pragma unroll
         for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
       }
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int v = 0; v < M; ++v) q[k][v] = fma(-dtR, acc[k][v], uu[v]);
+      for (int v = 0; v < M; ++v) q[k][v] = acc[k][v];
   }
 
   // Time averages of the final iterate and of its fluxes.

@@ -1,0 +1,91 @@
+"""Parity at the bench's full size (3D Euler N=5, base 27^3, two levels around
+the bubble: 268,087 cells), in the launch configuration the bench times
+(ader_step on the two prioritised streams).  The oracle cannot run the whole
+mesh in seconds, so it evaluates sampled cells one by one (step_sample) on its
+own independently built mesh; a conservation property is checked on all
+cells."""
+import numpy as np
+import pytest
+
+from oracle import ader as oader, basis as obasis, mesh as omesh, pde as opde, step as ostep
+import workloads
+from gpu_helpers import lib_keys, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+DIM, ORDER, BASE, LEVELS, RADIUS = 3, 5, 27, 2, 0.15
+
+
+@pytest.fixture(scope="module")
+def full_problem():
+    B = obasis.Basis(ORDER)
+    om = omesh.Mesh(DIM, (BASE,) * DIM, LEVELS)
+    center = workloads.sphere_center(0.0)
+    flag_seq = []
+    for _ in range(LEVELS):
+        fl = omesh.sphere_flags(om, center, RADIUS)
+        flag_seq.append(fl)
+        om.remesh(np.zeros((len(om.cells), 1, 2, 2, 2)), fl, obasis.Basis(1))
+    X = om.node_coords(B.xi)
+    u = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X), 0, 1))
+    del X
+    return om, B, u
+
+
+def lib_solver(precision, om):
+    from paper_1806_07984_gb300 import Solver
+    s = Solver(DIM, ORDER, "euler", base=(BASE,) * 3, max_level=LEVELS,
+               cfl=workloads.ADER_CFL[ORDER], precision=precision)
+    center = workloads.sphere_center(0.0)
+    ref = omesh.Mesh(DIM, (BASE,) * DIM, LEVELS)
+    for _ in range(LEVELS):
+        fl = s.sphere_flags(center, RADIUS)
+        fo = omesh.sphere_flags(ref, center, RADIUS)
+        perm = [ref.index[k] for k in lib_keys(s)]
+        assert np.array_equal(fl, fo[perm])          # host criterion agrees
+        s.remesh(fl)
+        ref.remesh(np.zeros((len(ref.cells), 1, 2, 2, 2)), fo, obasis.Basis(1))
+    s.classify(s.sphere_flags(center, RADIUS))
+    keys = lib_keys(s)
+    assert sorted(keys) == om.cells                  # same adaptive mesh
+    return s, np.array([om.index[k] for k in keys])
+
+
+def integrals(u, h, B):
+    y = u
+    for _ in range(DIM):
+        y = np.tensordot(y, B.w, axes=([y.ndim - 1], [0]))
+    return (y * np.prod(h, axis=1)[:, None]).sum(axis=0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_full_size_sampled_parity(full_problem, precision, tol):
+    om, B, u = full_problem
+    P = opde.Euler(DIM)
+    h = om.cell_widths()
+    dt = oader.cfl_dt(u, h, P, ORDER, cfl=workloads.ADER_CFL[ORDER])
+    s, perm = lib_solver(precision, om)
+    assert s.ncells == len(om.cells) == 268087
+    s.set_state(u[perm])
+    s.set_dt(dt)
+    s.step(1)
+    got = s.get_state().cpu().numpy()
+    assert s.status() == 0
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    # sampled cells: skeleton (both sides of transitions), enclave, first/last
+    rng = np.random.default_rng(5)
+    skel = np.flatnonzero(s.skeleton())
+    encl = np.flatnonzero(~s.skeleton().astype(bool))
+    lib_t = np.concatenate([rng.choice(skel, 12, replace=False), rng.choice(encl, 12, replace=False),
+                            [0, s.ncells - 1]])
+    or_t = perm[lib_t]
+    ref = ostep.step_sample(om, u, dt, P, B, or_t)
+    for a, b in zip(got[lib_t], ref):
+        assert rel_l2(a, b) < tol
+    assert rel_l2(got[lib_t] - u[or_t], ref - u[or_t]) < max(tol * 1e3, 1e-9)
+    # conservation over the whole mesh (periodic domain, hanging faces)
+    I0 = integrals(u, h, B)
+    I1 = integrals(got, h[perm], B)
+    assert np.allclose(I1, I0, rtol=0, atol=1e-11), I1 - I0
+    s.close()

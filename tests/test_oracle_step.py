@@ -181,3 +181,22 @@ def test_cfl_table(N):
     assert stability.spectral_radius(N, workloads.ADER_CFL[N]) <= 1.0 + 1e-9 or N >= 4
     assert stability.spectral_radius(N, workloads.ADER_CFL[N]) <= 1.0 + 1e-4
     assert stability.spectral_radius(N, 1.1 * nu) > 1.0 + 1e-4
+
+
+@pytest.mark.parametrize("which,N", [("amr2d", 3), ("amr3d", 2)])
+def test_step_sample_equals_full_step(which, N, request):
+    """The cell-by-cell evaluation used for full-size parity agrees with the
+    full oracle step on every kind of cell (conforming, coarse and fine sides
+    of transitions)."""
+    m = request.getfixturevalue(which)
+    B = basis.Basis(N)
+    P = pdes.Euler(m.dim)
+    u = random_state(m, B, "euler", seed=77)
+    dt = ader.cfl_dt(u, m.cell_widths(), P, N)
+    full = stepmod.step(m, u, dt, P, B)
+    skel = np.flatnonzero(m.skeleton())
+    rng = np.random.default_rng(0)
+    targets = np.concatenate([rng.choice(skel, 6, replace=False),
+                              rng.choice(len(m.cells), 6, replace=False)])
+    got = stepmod.step_sample(m, u, dt, P, B, targets)
+    assert np.abs(got - full.u[targets]).max() < 1e-13
