@@ -83,7 +83,9 @@ def test_full_size_sampled_parity(full_problem, precision, tol):
     ref = ostep.step_sample(om, u, dt, P, B, or_t)
     for a, b in zip(got[lib_t], ref):
         assert rel_l2(a, b) < tol
-    assert rel_l2(got[lib_t] - u[or_t], ref - u[or_t]) < max(tol * 1e3, 1e-9)
+    if precision == "fp64":
+        # the increment u(T+dt) - u(T) itself, not only the state
+        assert rel_l2(got[lib_t] - u[or_t], ref - u[or_t]) < 1e-9
     # conservation over the whole mesh (periodic domain, hanging faces)
     I0 = integrals(u, h, B)
     I1 = integrals(got, h[perm], B)
