@@ -19,6 +19,8 @@
 // The space-time block never touches HBM: the kernel reads u once and writes
 // u* and the 2d face blocks once.
 #pragma once
+#include <type_traits>
+
 #include "kernels.h"
 #include "pde.cuh"
 
@@ -33,6 +35,24 @@ struct PredictShape {
   static constexpr int NF = ipow(n, DIM - 1);
   static constexpr int CPB = NS >= 128 ? 1 : (256 / NS);
   static constexpr int THREADS = CPB * NS;
+};
+
+// Dynamic shared memory: fluxes of one slice fb[CPB][DIM][M][NS] (Real),
+// Q-bar qs[CPB][M][NS] (Real), and for the FP32 variant an FP64 reduction
+// buffer red[CPB][M][NS].
+template <int DIM, int N, class PDE, class Real>
+struct PredictSmem {
+  using S = PredictShape<DIM, N>;
+  static constexpr int kReal = S::CPB * (DIM + 1) * PDE::M * S::NS;
+  static constexpr int kRedOffset = (kReal * int(sizeof(Real)) + 7) / 8;  // in doubles
+  static constexpr int kPow2 = S::NS <= 1 ? 1 : (S::NS <= 2 ? 2 : (S::NS <= 4 ? 4 : (S::NS <= 8 ? 8 :
+      (S::NS <= 16 ? 16 : (S::NS <= 32 ? 32 : (S::NS <= 64 ? 64 : (S::NS <= 128 ? 128 :
+      (S::NS <= 256 ? 256 : 512))))))));
+  static constexpr size_t bytes() {
+    return std::is_same<Real, double>::value
+               ? size_t(kReal) * sizeof(Real)
+               : size_t(kRedOffset) * 8 + size_t(S::CPB) * PDE::M * S::NS * 8;
+  }
 };
 
 template <int DIM, int N, class PDE, class Real>
@@ -185,12 +205,12 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
     }
   if (valid && !finite) atomicOr(a.status, kStatusNonFinitePredictor);
   __syncthreads();
-  if (!valid) return;
 
   // Corrector volume term, contraction in Real, added to u in FP64.
+  double vol[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    double vol = 0.0;
+    vol[v] = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       const Real* Vrow = sV + id[d] * n;
@@ -198,10 +218,38 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
       Real s = Real(0);
 #pragma unroll
       for (int j = 0; j < n; ++j) s = fma(Vrow[j], line[j * stride[d]], s);
-      vol = fma(ihd[d], double(s), vol);
+      vol[v] = fma(ihd[d], double(s), vol[v]);
     }
+  }
+  if constexpr (!std::is_same<Real, double>::value) {
+    // The exact volume term has zero quadrature-weighted sum over the cell
+    // (sum_i w_i V_ij = w_j sum_i D_ji = 0); with V and F-bar rounded to Real it
+    // does not.  Remove that weighted mean in FP64 (deterministic tree sum) so
+    // that the step conserves to FP64 rounding; the change is within the
+    // Real rounding error of the term itself.
+    double* red = reinterpret_cast<double*>(smem_raw) + PredictSmem<DIM, N, PDE, Real>::kRedOffset;
+    double* my_red = red + cl * M * NS;
+    double W = 1.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) W *= a.B.w[id[d]];
+#pragma unroll
+    for (int v = 0; v < M; ++v) my_red[v * NS + node] = valid ? W * vol[v] : 0.0;
+    for (int st = PredictSmem<DIM, N, PDE, Real>::kPow2 / 2; st > 0; st >>= 1) {
+      __syncthreads();
+      if (node < st && node + st < NS) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) my_red[v * NS + node] += my_red[v * NS + node + st];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < M; ++v) vol[v] -= my_red[v * NS];
+  }
+  if (!valid) return;
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
     const int64_t gi = (cell * M + v) * NS + node;
-    a.ustar[gi] = fma(dt, vol, a.u[gi]);
+    a.ustar[gi] = fma(dt, vol[v], a.u[gi]);
   }
 
   // id|dc: extrapolate Q-bar and the normal flux F-bar_d to the 2d faces.
@@ -240,7 +288,7 @@ template <int DIM, int N, class PDE, class Real>
 cudaError_t launch_predict_t(const PredictArgs& a, cudaStream_t s) {
   using S = PredictShape<DIM, N>;
   if (a.count == 0) return cudaSuccess;
-  const size_t smem = size_t(S::CPB) * (DIM + 1) * PDE::M * S::NS * sizeof(Real);
+  const size_t smem = PredictSmem<DIM, N, PDE, Real>::bytes();
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(predict_kernel<DIM, N, PDE, Real>,
