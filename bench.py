@@ -35,6 +35,15 @@ METRIC = "3D Euler ADER-DG DoF-updates/s on 1 GB300; mixed vs FP64 at same L2 er
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (nominal); a pure DFMA loop measured 1.20
 FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 128 FP32 lanes/SM, FMA = 2 flops
 
+# DRAM bytes (read + write) per cell of one predictor launch, from the ncu
+# captures summarised in profiles/ for the current kernel versions (small
+# case of the same kernel, scaled by cells; per-cell traffic is size
+# independent).  A kernel change invalidates its entry.
+NCU_TRAFFIC_PER_CELL = {
+    "predict_kernel<3,5,Euler,double>": (173.242624e6 + 454.181376e6) / 19683,
+    "predict_kernel<3,5,Euler,float>": (170.238464e6 + 452.787968e6) / 19683,
+}
+
 WORKLOADS = {
     "euler3d-n5-amr": dict(dim=3, order=5, base=27, max_level=2, radius=0.15, remesh_every=10,
                            init="bubble"),
@@ -358,10 +367,12 @@ def main():
     bytes_ = predictor_bytes_per_cell(s.dim, s.order, s.nvar) * s.ncells
     peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
     achieved = flops / t_pred / 1e12
+    kname = (f"predict_kernel<{s.dim},{s.order},Euler,"
+             f"{'double' if args.precision == 'fp64' else 'float'}>")
+    tpc = NCU_TRAFFIC_PER_CELL.get(kname)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": f"predict_kernel<{s.dim},{s.order},Euler,"
-                          f"{'double' if args.precision == 'fp64' else 'float'}>",
+                "frac": achieved / peak, "traffic": tpc * s.ncells if tpc else None,
+                "kernel": kname,
                 "launch_ms": t_pred * 1e3, "algorithmic_flops": flops,
                 "algorithmic_bytes": bytes_, "hbm_gbs": bytes_ / t_pred / 1e9}
 
