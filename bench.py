@@ -210,6 +210,59 @@ def l2_error_vs_exact(s, u_dev, t):
     return [e / nv for e, nv in zip(errs, norms)], got
 
 
+def batch_state(sides, orders, specs):
+    """Concatenated vortex states of the batch in the library layout."""
+    parts = []
+    for side, order, sp in zip(sides, orders, specs):
+        n = order + 1
+        xi = (np.polynomial.legendre.leggauss(n)[0] + 1.0) / 2.0
+        c = np.arange(side * side)
+        cx, cy = (c % side).astype(np.float64), (c // side).astype(np.float64)
+        X = (cx[:, None, None] + xi[None, None, :]) / side + 0 * xi[None, :, None]
+        Y = (cy[:, None, None] + xi[None, :, None]) / side + 0 * xi[None, None, :]
+        q = workloads.isentropic_vortex(X, Y, center=sp["center"], eps=sp["eps"])
+        parts.append(np.ascontiguousarray(np.moveaxis(q, 0, 1)).ravel())
+    return np.concatenate(parts)
+
+
+def run_batched(torch, precision, steps, warmup, count=512):
+    """512 seeded 2D Euler instances (sides 9..81, orders 3..7, random
+    vortices) advanced by one CUDA-graph launch of persistent phase kernels."""
+    from paper_1806_07984_gb300 import ader as A
+    specs = workloads.batch_instances(count, seed=0)
+    sides = [sp["side"] for sp in specs]
+    orders = [sp["order"] for sp in specs]
+    cfg = A.ader_batch_config()
+    cfg.dim, cfg.pde, cfg.gamma, cfg.picard_iters = 2, A.ADER_EULER, workloads.GAMMA, 0
+    cfg.prec = A.ADER_FP64 if precision == "fp64" else A.ADER_FP32
+    b = A.ader_batch_init(cfg, sides, orders, [workloads.ADER_CFL[o] for o in orders])
+    u = torch.from_numpy(batch_state(sides, orders, specs)).cuda()
+    A.ader_batch_set_state(b, u.data_ptr(), True)
+    A.ader_batch_compute_dt(b)
+    bps, tile, tune_ms = A.ader_batch_tune(b)
+    A.ader_batch_run(b, warmup)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = A.ader_batch_launch_count(b)
+    e0.record(st)
+    A.ader_batch_run(b, steps, st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    launches = A.ader_batch_launch_count(b) - l0
+    status = A.ader_batch_status_word(b)
+    dofs = sum(s * s * 4 * (o + 1) ** 2 for s, o in zip(sides, orders))
+    A.ader_batch_destroy(b)
+    return {"workload": f"{count} 2D Euler instances, sides 9..81, orders 3..7, seed 0",
+            "precision": precision, "value": dofs * steps / el, "unit": "DoF-updates/s",
+            "steps": steps, "ms_per_step": el / steps * 1e3, "dofs": dofs,
+            "cells": sum(s * s for s in sides), "graph_launches": 1,
+            "kernel_launches": launches, "tuned": {"ctas_per_sm": bps, "tile": tile,
+                                                   "step_ms": tune_ms}, "status": status}
+
+
 def time_predictor(s, torch, reps=3):
     """Average duration of one ader_predict(ADER_ALL) launch, CUDA events on
     the launching stream."""
@@ -309,6 +362,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -421,6 +475,12 @@ def main():
         s.close()
         del u_dev
 
+    # ---- batched instances (one CUDA graph per run) --------------------------
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = {"fp64": run_batched(torch, "fp64", 20, 2),
+                   "fp32": run_batched(torch, "fp32", 20, 2)}
+
     # ---- end to end through the public API with host buffers ---------------
     # Every step: H2D of the state from pinned host memory, one step, D2H of
     # the new state into pinned host memory (the step's result).
@@ -467,7 +527,7 @@ def main():
                        "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
                        "remesh_every": wl["remesh_every"]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
-            "clocks": clk, "mixed": mixed}
+            "clocks": clk, "mixed": mixed, "batched": batched}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
     if rank == 0:

@@ -183,6 +183,59 @@ ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
 /* Number of kernel launches this context has enqueued so far. */
 ader_status ader_launch_count(ader_ctx* ctx, int64_t* out);
 
+/* ---- Batched instances ---------------------------------------------------
+ * Many independent problems of uneven sizes and orders advanced together
+ * (Algorithm 1 per instance, each instance with its own global time step).
+ * Instance i is a uniform periodic grid of sides[i]^2 cells on the unit
+ * square with order orders[i] and Courant factor cfls[i].  Its state is the
+ * block u[offsets[i] .. offsets[i+1]) of one concatenated FP64 array, laid
+ * out like a context's state.  Every phase of a step (predictor, Riemann,
+ * corrector, dt update) is one persistent kernel whose CTAs pull work items
+ * (instance, tile of cells or faces) from a queue -- the consumer tasks of
+ * Algorithm 2 on CTAs -- and ader_batch_run launches all steps as one CUDA
+ * graph.  Currently 2D Euler. */
+typedef struct {
+  int dim;           /* 2 */
+  ader_pde pde;      /* ADER_EULER */
+  double gamma;
+  int picard_iters;  /* 0 selects order + 1 per instance */
+  ader_precision prec;
+} ader_batch_config;
+
+typedef struct ader_batch ader_batch;
+
+ader_status ader_batch_init(const ader_batch_config* cfg, int ninst, const int* sides,
+                            const int* orders, const double* cfls, ader_batch** out);
+void ader_batch_destroy(ader_batch* b);
+const char* ader_batch_last_error(ader_batch* b);
+
+/* offsets[0..ninst] (host, int64) of each instance's state in doubles. */
+ader_status ader_batch_offsets(ader_batch* b, int64_t* offsets);
+
+/* Concatenated state in/out (on_device: device pointer, else host). */
+ader_status ader_batch_set_state(ader_batch* b, const double* u, int on_device, void* stream);
+ader_status ader_batch_get_state(ader_batch* b, double* u, int on_device, void* stream);
+
+/* dt of every instance from its current state (device-resident). */
+ader_status ader_batch_compute_dt(ader_batch* b, void* stream);
+/* Copy the per-instance dt (of the next step) to the host (synchronises). */
+ader_status ader_batch_get_dt(ader_batch* b, double* dt_host);
+
+/* Launch shape: persistent CTAs per SM and tile factor (cells per work item =
+ * tile x cells per CTA pass). */
+ader_status ader_batch_set_launch(ader_batch* b, int blocks_per_sm, int tile);
+
+/* Autotuner: times one step for every (CTAs per SM, tile in {1,2,4,8}) that
+ * fits, keeps the fastest, restores the state.  Synchronises. */
+ader_status ader_batch_tune(ader_batch* b, int* blocks_per_sm, int* tile, float* ms_per_step);
+
+/* nsteps steps of every instance as one CUDA graph launch on `stream`. */
+ader_status ader_batch_run(ader_batch* b, int nsteps, void* stream);
+
+/* Status word as in ader_status_word (synchronises, clears). */
+ader_status ader_batch_status_word(ader_batch* b, uint32_t* out);
+ader_status ader_batch_launch_count(ader_batch* b, int64_t* out);
+
 /* ---- Allocation-free time step ------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory: code running inside a memory pool or arena

@@ -30,7 +30,11 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_correct", "ader_step", "ader_remesh", "ader_classify", "ader_sphere_flags",
            "ader_status_word", "ader_launch_count", "ader_mesh_create", "ader_mesh_destroy",
            "ader_mesh_adapt", "ader_mesh_sizes", "ader_mesh_leaves", "ader_mesh_faces",
-           "ader_mesh_sphere_flags", "ader_compute_dt_static"]
+           "ader_mesh_sphere_flags", "ader_compute_dt_static", "ader_batch_init",
+           "ader_batch_destroy", "ader_batch_last_error", "ader_batch_offsets",
+           "ader_batch_set_state", "ader_batch_get_state", "ader_batch_compute_dt",
+           "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
+           "ader_batch_status_word", "ader_batch_launch_count"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -38,6 +42,11 @@ class AderError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {detail}".strip())
+
+
+class ader_batch_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("pde", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int)]
 
 
 class ader_config(ctypes.Structure):
@@ -91,6 +100,21 @@ def lib():
         "ader_mesh_leaves": ([_vp, _vp, _vp], ctypes.c_int),
         "ader_mesh_faces": ([_vp, _vp, _vp, _vp], ctypes.c_int),
         "ader_mesh_sphere_flags": ([_vp, _vp, ctypes.c_double, _vp, _vp, _vp], ctypes.c_int),
+        "ader_batch_init": ([ctypes.POINTER(ader_batch_config), ctypes.c_int, _vp, _vp, _vp,
+                             ctypes.POINTER(_vp)], ctypes.c_int),
+        "ader_batch_destroy": ([_vp], None),
+        "ader_batch_last_error": ([_vp], ctypes.c_char_p),
+        "ader_batch_offsets": ([_vp, _vp], ctypes.c_int),
+        "ader_batch_set_state": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_batch_get_state": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_batch_compute_dt": ([_vp, _vp], ctypes.c_int),
+        "ader_batch_get_dt": ([_vp, _vp], ctypes.c_int),
+        "ader_batch_set_launch": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "ader_batch_tune": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "ader_batch_run": ([_vp, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_batch_status_word": ([_vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "ader_batch_launch_count": ([_vp, _i64p], ctypes.c_int),
         "ader_compute_dt_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
                                     _vp], ctypes.c_int),
@@ -295,3 +319,75 @@ def ader_compute_dt_static(dim, order, pde, gamma, cfl, base, lo, hi, ncells, u_
     _check(None, lib().ader_compute_dt_static(dim, order, pde, gamma, cfl, _ptr(b), _ptr(lo_),
                                               _ptr(hi_), ncells, _ptr(u_dev), _ptr(level_dev),
                                               _ptr(dt_dev), stream), "ader_compute_dt_static")
+
+
+# ---- batched instances ------------------------------------------------------
+def _bcheck(b, status, where):
+    if status != ADER_OK:
+        detail = lib().ader_batch_last_error(b).decode() if b else ""
+        raise AderError(status, where, detail)
+
+
+def ader_batch_init(cfg, sides, orders, cfls):
+    sides = np.ascontiguousarray(sides, dtype=np.int32)
+    orders = np.ascontiguousarray(orders, dtype=np.int32)
+    cfls = np.ascontiguousarray(cfls, dtype=np.float64)
+    b = _vp()
+    _bcheck(None, lib().ader_batch_init(ctypes.byref(cfg), len(sides), _ptr(sides), _ptr(orders),
+                                        _ptr(cfls), ctypes.byref(b)), "ader_batch_init")
+    return b
+
+
+def ader_batch_destroy(b):
+    lib().ader_batch_destroy(b)
+
+
+def ader_batch_offsets(b, ninst):
+    out = np.zeros(ninst + 1, dtype=np.int64)
+    _bcheck(b, lib().ader_batch_offsets(b, _ptr(out)), "ader_batch_offsets")
+    return out
+
+
+def ader_batch_set_state(b, u, on_device, stream=None):
+    _bcheck(b, lib().ader_batch_set_state(b, _ptr(u), int(on_device), stream), "ader_batch_set_state")
+
+
+def ader_batch_get_state(b, u, on_device, stream=None):
+    _bcheck(b, lib().ader_batch_get_state(b, _ptr(u), int(on_device), stream), "ader_batch_get_state")
+
+
+def ader_batch_compute_dt(b, stream=None):
+    _bcheck(b, lib().ader_batch_compute_dt(b, stream), "ader_batch_compute_dt")
+
+
+def ader_batch_get_dt(b, ninst):
+    out = np.zeros(ninst, dtype=np.float64)
+    _bcheck(b, lib().ader_batch_get_dt(b, _ptr(out)), "ader_batch_get_dt")
+    return out
+
+
+def ader_batch_set_launch(b, blocks_per_sm, tile):
+    _bcheck(b, lib().ader_batch_set_launch(b, blocks_per_sm, tile), "ader_batch_set_launch")
+
+
+def ader_batch_tune(b):
+    bps, tile, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _bcheck(b, lib().ader_batch_tune(b, ctypes.byref(bps), ctypes.byref(tile), ctypes.byref(ms)),
+            "ader_batch_tune")
+    return bps.value, tile.value, ms.value
+
+
+def ader_batch_run(b, nsteps, stream=None):
+    _bcheck(b, lib().ader_batch_run(b, nsteps, stream), "ader_batch_run")
+
+
+def ader_batch_status_word(b):
+    v = ctypes.c_uint32()
+    _bcheck(b, lib().ader_batch_status_word(b, ctypes.byref(v)), "ader_batch_status_word")
+    return v.value
+
+
+def ader_batch_launch_count(b):
+    v = ctypes.c_int64()
+    _bcheck(b, lib().ader_batch_launch_count(b, ctypes.byref(v)), "ader_batch_launch_count")
+    return v.value

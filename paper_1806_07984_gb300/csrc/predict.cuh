@@ -55,57 +55,57 @@ struct PredictSmem {
   }
 };
 
+// One pass of the predictor over CPB cells of one CTA.  Thread t < CPB*NS
+// works on cell t / NS, node t % NS; further threads of the CTA only join
+// the barriers.  `cell` is the cell index (relative to the field pointers) of
+// this thread's cell and `valid` whether it exists; `ihd` its 1/h_d.  Every
+// thread of the CTA must call this with the same dt, B and iters.
 template <int DIM, int N, class PDE, class Real>
-__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
-    predict_kernel(const PredictArgs a) {
+__device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, double gamma_d,
+                                              int iters, uint32_t* status, const double* u_in,
+                                              double* ustar, double* faceQ, double* faceF,
+                                              int64_t cell, bool valid, const double (&ihd)[DIM],
+                                              unsigned char* smem_raw) {
   using S = PredictShape<DIM, N>;
   constexpr int n = S::n, NS = S::NS, NF = S::NF, CPB = S::CPB, M = PDE::M;
   // sDh[c][d]: D scaled by 1/h_d of cell c; sMd = -dt Mt; sRs[k] = sum_l sMd[k][l]
   __shared__ Real sDh[CPB][DIM][n * n], sMd[n * n], sRs[n], sV[n * n], sw[n], sp0[n], sp1[n];
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   // fb[CPB][DIM][M][NS] fluxes of one slice (later F-bar); qs[CPB][M][NS] Q-bar
   Real* fb = reinterpret_cast<Real*>(smem_raw);
   Real* qs = fb + CPB * DIM * M * NS;
 
   const int tid = threadIdx.x;
-  const double dt = *a.dt;
+  const bool active = tid < CPB * NS;
+  __syncthreads();  // a previous pass of this CTA may still read the shared tables
   for (int t = tid; t < n * n; t += blockDim.x) {
-    sMd[t] = Real(-dt * a.B.Mt[t / n][t % n]);
-    sV[t] = Real(a.B.V[t / n][t % n]);
+    sMd[t] = Real(-dt * B.Mt[t / n][t % n]);
+    sV[t] = Real(B.V[t / n][t % n]);
   }
   if (tid < n) {
     double r = 0.0;
-    for (int l = 0; l < n; ++l) r += a.B.Mt[tid][l];
+    for (int l = 0; l < n; ++l) r += B.Mt[tid][l];
     sRs[tid] = Real(-dt * r);
-    sw[tid] = Real(a.B.w[tid]);
-    sp0[tid] = Real(a.B.phi0[tid]);
-    sp1[tid] = Real(a.B.phi1[tid]);
+    sw[tid] = Real(B.w[tid]);
+    sp0[tid] = Real(B.phi0[tid]);
+    sp1[tid] = Real(B.phi1[tid]);
   }
 
-  const int cl = tid / NS;
-  const int node = tid - cl * NS;
-  const int64_t slot = int64_t(blockIdx.x) * CPB + cl;
-  const bool valid = slot < a.count;
-  const int64_t cell = valid ? int64_t(a.cells[slot]) : 0;
+  const int cl = active ? tid / NS : 0;
+  const int node = active ? tid - cl * NS : 0;
+  valid = valid && active;
 
   int id[3] = {node % n, (node / n) % n, node / (n * n)};
   const int stride[3] = {1, n, n * n};
-  double ihd[DIM];
-  {
-    const int lv = valid ? int(a.level[cell]) : 0;
+  if (active && node < n * n) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) ihd[d] = a.inv_h[lv][d];
+    for (int d = 0; d < DIM; ++d) sDh[cl][d][node] = Real(B.D[node / n][node % n] * ihd[d]);
   }
-  if (node < n * n) {
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) sDh[cl][d][node] = Real(a.B.D[node / n][node % n] * ihd[d]);
-  }
-  const Real gamma = Real(a.gamma);
+  const Real gamma = Real(gamma_d);
 
   Real uu[M];
 #pragma unroll
   for (int v = 0; v < M; ++v)
-    uu[v] = valid ? Real(a.u[(cell * M + v) * NS + node]) : Real(v == 0 ? 1 : 0);
+    uu[v] = valid ? Real(u_in[(cell * M + v) * NS + node]) : Real(v == 0 ? 1 : 0);
   if (!valid && PDE::kPositivity) uu[M - 1] = Real(2.5);
 
   Real* my_fb = fb + cl * DIM * M * NS;
@@ -115,10 +115,12 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
   auto divergence = [&](const Real(&x)[M], Real(&g)[M]) {
     Real f[DIM][M];
     PDE::fluxes(x, f, gamma);
+    if (active) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d)
+      for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int v = 0; v < M; ++v) my_fb[(d * M + v) * NS + node] = f[d][v];
+        for (int v = 0; v < M; ++v) my_fb[(d * M + v) * NS + node] = f[d][v];
+    }
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < M; ++v) g[v] = Real(0);
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
 #pragma unroll
       for (int v = 0; v < M; ++v) q[k][v] = fma(sRs[k], g[v], uu[v]);
   }
-  for (int r = 1; r < a.iters; ++r) {
+  for (int r = 1; r < iters; ++r) {
     Real acc[n][M];
 #pragma unroll
     for (int k = 0; k < n; ++k)
@@ -194,16 +196,16 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
 #pragma unroll
   for (int v = 0; v < M; ++v) {
     finite = finite && isfinite(qb[v]);
-    my_qs[v * NS + node] = qb[v];
+    if (active) my_qs[v * NS + node] = qb[v];
   }
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       finite = finite && isfinite(Fb[d][v]);
-      my_fb[(d * M + v) * NS + node] = Fb[d][v];
+      if (active) my_fb[(d * M + v) * NS + node] = Fb[d][v];
     }
-  if (valid && !finite) atomicOr(a.status, kStatusNonFinitePredictor);
+  if (valid && !finite) atomicOr(status, kStatusNonFinitePredictor);
   __syncthreads();
 
   // Corrector volume term, contraction in Real, added to u in FP64.
@@ -231,12 +233,14 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
     double* my_red = red + cl * M * NS;
     double W = 1.0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) W *= a.B.w[id[d]];
+    for (int d = 0; d < DIM; ++d) W *= B.w[id[d]];
+    if (active) {
 #pragma unroll
-    for (int v = 0; v < M; ++v) my_red[v * NS + node] = valid ? W * vol[v] : 0.0;
+      for (int v = 0; v < M; ++v) my_red[v * NS + node] = valid ? W * vol[v] : 0.0;
+    }
     for (int st = PredictSmem<DIM, N, PDE, Real>::kPow2 / 2; st > 0; st >>= 1) {
       __syncthreads();
-      if (node < st && node + st < NS) {
+      if (active && node < st && node + st < NS) {
 #pragma unroll
         for (int v = 0; v < M; ++v) my_red[v * NS + node] += my_red[v * NS + node + st];
       }
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
 #pragma unroll
   for (int v = 0; v < M; ++v) {
     const int64_t gi = (cell * M + v) * NS + node;
-    a.ustar[gi] = fma(dt, vol[v], a.u[gi]);
+    ustar[gi] = fma(dt, vol[v], u_in[gi]);
   }
 
   // id|dc: extrapolate Q-bar and the normal flux F-bar_d to the 2d faces.
@@ -277,11 +281,28 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
           sq = fma(phi[j], lq[j * stride[d]], sq);
           sf = fma(phi[j], lf[j * stride[d]], sf);
         }
-        a.faceQ[fo + v * NF] = double(sq);
-        a.faceF[fo + v * NF] = double(sf);
+        faceQ[fo + v * NF] = double(sq);
+        faceF[fo + v * NF] = double(sf);
       }
     }
   }
+}
+
+template <int DIM, int N, class PDE, class Real>
+__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
+    predict_kernel(const PredictArgs a) {
+  using S = PredictShape<DIM, N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cl = threadIdx.x / S::NS;
+  const int64_t slot = int64_t(blockIdx.x) * S::CPB + cl;
+  const bool valid = slot < a.count;
+  const int64_t cell = valid ? int64_t(a.cells[slot]) : 0;
+  double ihd[DIM];
+  const int lv = valid ? int(a.level[cell]) : 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) ihd[d] = a.inv_h[lv][d];
+  predict_cells<DIM, N, PDE, Real>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u, a.ustar, a.faceQ,
+                                   a.faceF, cell, valid, ihd, smem_raw);
 }
 
 template <int DIM, int N, class PDE, class Real>
