@@ -186,16 +186,19 @@ __device__ __forceinline__ void batch_correct_item(const BatchArgs& a, const Bat
       for (int v = 0; v < M; ++v) q[v] = a.u[in.u_off + (cell * M + v) * NS + node];
     }
     bool ok_all = true;
+    double node_rate = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       bool ok;
-      rate += PDE::max_speed(q, d, a.gamma, &ok) * in.inv_h;
+      node_rate += PDE::max_speed(q, d, a.gamma, &ok) * in.inv_h;
       ok_all = ok_all && ok;
     }
     if (!ok_all) {
       atomicOr(a.status, kStatusNonPhysical);
-      rate = __longlong_as_double(0x7ff8000000000000ll);
+      node_rate = __longlong_as_double(0x7ff8000000000000ll);
     }
+    // maximum over the passes of this item (NaN, a non-physical state, sticks)
+    rate = (node_rate != node_rate || rate != rate) ? node_rate + rate : fmax(rate, node_rate);
   }
   block_max_to(rate, a.rate + w.inst);
 }
