@@ -263,6 +263,59 @@ def run_batched(torch, precision, steps, warmup, count=512):
                                                    "step_ms": tune_ms}, "status": status}
 
 
+def run_adjoint(torch):
+    """3D linear acoustics N=4 on 27^3 (Picard 13 iterations, FP64): one loss
+    and gradient with respect to the initial state over 50 steps, 64 receivers,
+    checkpoints every 10 steps (forward + recomputation + adjoint sweep)."""
+    from paper_1806_07984_gb300 import Solver, adjoint as adj, ader as A
+    order = 4
+    s = Solver(3, order, "acoustics", base=(27, 27, 27), cfl=workloads.ADER_CFL[order],
+               picard_iters=3 * order + 1)
+    X = s.node_coords()
+    u0 = torch.from_numpy(np.ascontiguousarray(
+        np.moveaxis(workloads.acoustic_pulses(X, seed=1), 0, 1))).cuda()
+    uobs = torch.from_numpy(np.ascontiguousarray(
+        np.moveaxis(workloads.acoustic_pulses(X, seed=3), 0, 1))).cuda()
+    del X
+    s.set_state(u0)
+    s.compute_dt()
+    dt = s.dt.clone()
+    rec = adj.Receivers(s, workloads.acoustic_receivers(64, seed=2))
+    nsteps = 50
+    p_obs, _ = adj.forward_run(s, uobs, dt, rec, nsteps)
+    loss_fn = adj.AcousticMisfit.make(s, dt, rec, p_obs, nsteps, every=10)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    u = u0.clone().requires_grad_(True)
+    e0.record(st)
+    loss = loss_fn(u)
+    e1.record(st)
+    loss.backward()
+    e2.record(st)
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1) / 1e3
+    t_bwd = e1.elapsed_time(e2) / 1e3
+    # one adjoint step kernel sequence, timed alone
+    lam = torch.randn_like(u0)
+    out = torch.empty_like(u0)
+    A.ader_adjoint_step(s.ctx, lam, out, dt)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(5):
+        A.ader_adjoint_step(s.ctx, lam, out, dt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_adj = e0.elapsed_time(e1) / 5e3
+    dofs = s.ncells * s.nvar * s.n ** 3
+    s.close()
+    return {"workload": "3D acoustics N=4, 27^3 periodic, 50 steps, 64 receivers, checkpoints every 10",
+            "loss": float(loss), "grad_norm": float(u.grad.norm()),
+            "forward_s": t_fwd, "backward_s": t_bwd, "gradient_s": t_fwd + t_bwd,
+            "adjoint_step_ms": t_adj * 1e3, "adjoint_dof_updates_per_s": dofs / t_adj,
+            "dofs": dofs}
+
+
 def time_predictor(s, torch, reps=3):
     """Average duration of one ader_predict(ADER_ALL) launch, CUDA events on
     the launching stream."""
@@ -363,6 +416,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -481,6 +535,8 @@ def main():
         batched = {"fp64": run_batched(torch, "fp64", 20, 2),
                    "fp32": run_batched(torch, "fp32", 20, 2)}
 
+    adjoint = run_adjoint(torch) if (not args.no_adjoint and world == 1) else None
+
     # ---- end to end through the public API with host buffers ---------------
     # Every step: H2D of the state from pinned host memory, one step, D2H of
     # the new state into pinned host memory (the step's result).
@@ -527,7 +583,7 @@ def main():
                        "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
                        "remesh_every": wl["remesh_every"]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
-            "clocks": clk, "mixed": mixed, "batched": batched}
+            "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
     if rank == 0:

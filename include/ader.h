@@ -180,6 +180,29 @@ ader_status ader_sphere_flags(ader_ctx* ctx, const double center[3], double radi
  * CFL rate, bit 3 bad transfer index); clears it. */
 ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
 
+/* Discrete adjoint of one step: *lambda_out = A^T lambda_in, where A is the
+ * linear map u(T) -> u(T+dt) of ader_step/ader_predict+ader_riemann+
+ * ader_correct for linear acoustics (ADER_ACOUSTICS) with the dt stored at
+ * dt_dev.  Each task of Eq. (4) is transposed in reverse order (corrector
+ * lifting, Rusanov with s = c = 1, predictor volume term and face
+ * extrapolation, time averages, and the Picard iterations unrolled with the
+ * forward count).  Needs a mesh without resolution transitions; lambda
+ * arrays are device [c][var][node] and must not alias.  Uses the context's
+ * face buffers as scratch. */
+ader_status ader_adjoint_step(ader_ctx* ctx, const double* lambda_in, double* lambda_out,
+                              const double* dt_dev, void* stream);
+
+/* Point values of one variable: out[p] = sum_node weights[p][node]
+ * field[cells[p]][var][node] (device arrays; weights npts x (order+1)^dim, the
+ * Lagrange basis at each point's reference coordinates).  field NULL samples
+ * the context's state.  ader_sample_adjoint adds the transpose:
+ * field[cells[p]][var][node] += weights[p][node] values[p], points in order. */
+ader_status ader_sample(ader_ctx* ctx, int npts, const int32_t* cells, const double* weights,
+                        int var, const double* field, double* out, void* stream);
+ader_status ader_sample_adjoint(ader_ctx* ctx, int npts, const int32_t* cells,
+                                const double* weights, int var, const double* values,
+                                double* field, void* stream);
+
 /* Number of kernel launches this context has enqueued so far. */
 ader_status ader_launch_count(ader_ctx* ctx, int64_t* out);
 

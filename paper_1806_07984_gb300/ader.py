@@ -34,7 +34,8 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_batch_destroy", "ader_batch_last_error", "ader_batch_offsets",
            "ader_batch_set_state", "ader_batch_get_state", "ader_batch_compute_dt",
            "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
-           "ader_batch_status_word", "ader_batch_launch_count"]
+           "ader_batch_status_word", "ader_batch_launch_count", "ader_adjoint_step",
+           "ader_sample", "ader_sample_adjoint"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -115,6 +116,10 @@ def lib():
         "ader_batch_run": ([_vp, ctypes.c_int, _vp], ctypes.c_int),
         "ader_batch_status_word": ([_vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "ader_batch_launch_count": ([_vp, _i64p], ctypes.c_int),
+        "ader_adjoint_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "ader_sample": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+        "ader_sample_adjoint": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
+                                ctypes.c_int),
         "ader_compute_dt_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
                                     _vp], ctypes.c_int),
@@ -391,3 +396,20 @@ def ader_batch_launch_count(b):
     v = ctypes.c_int64()
     _bcheck(b, lib().ader_batch_launch_count(b, ctypes.byref(v)), "ader_batch_launch_count")
     return v.value
+
+
+# ---- adjoint and point sampling --------------------------------------------
+def ader_adjoint_step(ctx, lam_in, lam_out, dt_dev, stream=None):
+    _check(ctx, lib().ader_adjoint_step(ctx, _ptr(lam_in), _ptr(lam_out), _ptr(dt_dev), stream),
+           "ader_adjoint_step")
+
+
+def ader_sample(ctx, npts, cells_dev, weights_dev, var, field_dev, out_dev, stream=None):
+    _check(ctx, lib().ader_sample(ctx, npts, _ptr(cells_dev), _ptr(weights_dev), var,
+                                  _ptr(field_dev), _ptr(out_dev), stream), "ader_sample")
+
+
+def ader_sample_adjoint(ctx, npts, cells_dev, weights_dev, var, values_dev, field_dev, stream=None):
+    _check(ctx, lib().ader_sample_adjoint(ctx, npts, _ptr(cells_dev), _ptr(weights_dev), var,
+                                          _ptr(values_dev), _ptr(field_dev), stream),
+           "ader_sample_adjoint")

@@ -575,6 +575,57 @@ ader_status ader_status_word(ader_ctx* c, uint32_t* out) {
   return ADER_OK;
 }
 
+ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out,
+                              const double* dt_dev, void* stream) {
+  if (!c || !lam_in || !lam_out || !dt_dev || lam_in == lam_out) return ADER_ERR_ARG;
+  if (c->cfg.pde != ADER_ACOUSTICS) {
+    c->err = "the adjoint step is implemented for linear acoustics";
+    return ADER_ERR_ARG;
+  }
+  if (!c->tree.parents.empty()) {
+    c->err = "the adjoint step needs a mesh without resolution transitions";
+    return ADER_ERR_ARG;
+  }
+  AdjointArgs a{};
+  a.lam_in = lam_in;
+  a.lam_out = lam_out;
+  a.fstar_bar = c->fstar;
+  a.faceQ_bar = c->faceQ;
+  a.faceF_bar = c->faceF;
+  a.conf = c->conf;
+  a.nconf = int64_t(c->tree.conf.size());
+  a.level = c->level;
+  a.ncells = int64_t(c->tree.cells.size());
+  a.dt = dt_dev;
+  a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
+  a.B = c->B;
+  c->launches += 3;
+  CK(launch_adjoint(c->cfg.dim, c->cfg.order, a, static_cast<cudaStream_t>(stream)), "adjoint step");
+  return ADER_OK;
+}
+
+ader_status ader_sample(ader_ctx* c, int npts, const int32_t* cells, const double* weights, int var,
+                        const double* field, double* out, void* stream) {
+  if (!c || npts < 0 || (npts > 0 && (!cells || !weights || !out)) || var < 0 || var >= c->M)
+    return ADER_ERR_ARG;
+  c->launches += npts > 0 ? 1 : 0;
+  CK(launch_sample(field ? field : c->u, c->M, c->NS, var, npts, cells, weights, out,
+                   static_cast<cudaStream_t>(stream)), "sample");
+  return ADER_OK;
+}
+
+ader_status ader_sample_adjoint(ader_ctx* c, int npts, const int32_t* cells, const double* weights,
+                                int var, const double* values, double* field, void* stream) {
+  if (!c || npts < 0 || !field || (npts > 0 && (!cells || !weights || !values)) || var < 0 ||
+      var >= c->M)
+    return ADER_ERR_ARG;
+  c->launches += npts > 0 ? 1 : 0;
+  CK(launch_sample_adjoint(field, c->M, c->NS, var, npts, cells, weights, values,
+                           static_cast<cudaStream_t>(stream)), "sample adjoint");
+  return ADER_OK;
+}
+
 ader_status ader_launch_count(ader_ctx* c, int64_t* out) {
   if (!c || !out) return ADER_ERR_ARG;
   *out = c->launches;

@@ -95,4 +95,27 @@ cudaError_t launch_finalize_dt(unsigned long long* rate_max, double cfl, double*
                                uint32_t* status, cudaStream_t s);
 cudaError_t launch_transfer(int dim, int order, int nvar, const TransferArgs& a, cudaStream_t s);
 
+struct AdjointArgs {
+  const double* lam_in;   // lambda for u(T+dt)      [c][var][node]
+  double* lam_out;        // A^T lambda_in           [c][var][node]
+  double* fstar_bar;      // [c][2d][var][fnode] scratch
+  double* faceQ_bar;
+  double* faceF_bar;
+  const ConfFace* conf;
+  int64_t nconf;
+  const int8_t* level;
+  int64_t ncells;
+  const double* dt;
+  int iters;
+  double inv_h[kMaxLevels][3];
+  BasisTables B;
+};
+
+cudaError_t launch_adjoint(int dim, int order, const AdjointArgs& a, cudaStream_t s);
+cudaError_t launch_sample(const double* field, int M, int NS, int var, int npts,
+                          const int32_t* cells, const double* weights, double* out, cudaStream_t s);
+cudaError_t launch_sample_adjoint(double* field, int M, int NS, int var, int npts,
+                                  const int32_t* cells, const double* weights, const double* values,
+                                  cudaStream_t s);
+
 }  // namespace ader

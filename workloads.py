@@ -117,3 +117,9 @@ def batch_instances(count=512, seed=0):
                         center=tuple(rng.uniform(0.0, 1.0, size=2)),
                         eps=float(rng.uniform(1.0, 5.0))))
     return out
+
+
+def acoustic_receivers(count=64, seed=2, dim=3):
+    """Seeded receiver points in [0, 1)^dim."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.0, size=(count, dim))
