@@ -111,6 +111,20 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   Real* my_fb = fb + cl * DIM * M * NS;
   Real* my_qs = qs + cl * M * NS;
 
+  // FP32: this thread's rows of D/h_d live in registers for every slice
+  // (shared-memory bandwidth bounds that variant).  FP64: they stay in shared
+  // memory (the FP64 pipe bounds that variant and registers are scarce).
+  constexpr bool kDinRegs = !std::is_same<Real, double>::value;
+  constexpr int kDr = kDinRegs ? n : 1;
+  __syncthreads();
+  Real Dr[DIM][kDr];
+  if constexpr (kDinRegs) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int j = 0; j < kDr; ++j) Dr[d][j] = sDh[cl][d][id[d] * n + j];
+  }
+
   // g = sum_d (D/h_d)^(d) f_d(x) at this node, for the slice held in x.
   auto divergence = [&](const Real(&x)[M], Real(&g)[M]) {
     Real f[DIM][M];
@@ -126,13 +140,19 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     for (int v = 0; v < M; ++v) g[v] = Real(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      const Real* Drow = &sDh[cl][d][id[d] * n];
       const int base = node - id[d] * stride[d];
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         const Real* line = my_fb + (d * M + v) * NS + base;
 #pragma unroll
-        for (int j = 0; j < n; ++j) g[v] = fma(Drow[j], line[j * stride[d]], g[v]);
+        for (int j = 0; j < n; ++j) {
+          Real dj;
+          if constexpr (kDinRegs)
+            dj = Dr[d][j < kDr ? j : 0];
+          else
+            dj = sDh[cl][d][id[d] * n + j];
+          g[v] = fma(dj, line[j * stride[d]], g[v]);
+        }
       }
     }
     __syncthreads();
