@@ -143,6 +143,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+_U0_CACHE = {}
+
+
 def build_problem(wl, precision, device):
     from paper_1806_07984_gb300 import Solver
     dim, order = wl["dim"], wl["order"]
@@ -153,13 +156,16 @@ def build_problem(wl, precision, device):
         s.remesh(s.sphere_flags(center, wl["radius"]))
     if wl["max_level"] > 0:
         s.classify(s.sphere_flags(center, wl["radius"]))
-    X = s.node_coords()
-    if wl["init"] == "bubble":
-        u = workloads.density_bubble(X)
-    else:
-        u = workloads.isentropic_vortex(X[0], X[1])
-    u = np.ascontiguousarray(np.moveaxis(u, 0, 1))
-    return s, u
+    key = (id(wl), s.ncells)
+    if key not in _U0_CACHE:
+        X = s.node_coords()
+        if wl["init"] == "bubble":
+            u = workloads.density_bubble(X)
+        else:
+            u = workloads.isentropic_vortex(X[0], X[1])
+        _U0_CACHE.clear()
+        _U0_CACHE[key] = np.ascontiguousarray(np.moveaxis(u, 0, 1))
+    return s, _U0_CACHE[key]
 
 
 def dofs_of(s):
@@ -412,9 +418,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="euler3d-n5-amr", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "fp32", "tf32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed", default="fp32,tf32x3,bf16x3,tf32",
+                    help="predictor precisions compared with FP64 ('' to skip)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
@@ -475,8 +483,11 @@ def main():
     bytes_ = predictor_bytes_per_cell(s.dim, s.order, s.nvar) * s.ncells
     peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
     achieved = flops / t_pred / 1e12
-    kname = (f"predict_kernel<{s.dim},{s.order},Euler,"
-             f"{'double' if args.precision == 'fp64' else 'float'}>")
+    if args.precision in ("tf32", "tf32x3", "bf16x3"):
+        kname = f"predict_tc_kernel<{s.order},Euler,{args.precision}>"
+    else:
+        kname = (f"predict_kernel<{s.dim},{s.order},Euler,"
+                 f"{'double' if args.precision == 'fp64' else 'float'}>")
     tpc = NCU_TRAFFIC_PER_CELL.get(kname)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": tpc * s.ncells if tpc else None,
@@ -484,47 +495,59 @@ def main():
                 "launch_ms": t_pred * 1e3, "algorithmic_flops": flops,
                 "algorithmic_bytes": bytes_, "hbm_gbs": bytes_ / t_pred / 1e9}
 
-    # ---- mixed precision: FP32 predictor on the same workload -------------------
+    # ---- mixed precision: FP32 / tensor-core predictors on the same workload ----
     mixed = None
-    if args.precision == "fp64" and not args.no_mixed:
+    if args.precision == "fp64" and args.mixed:
         t_fp64 = float(t_dev.item())
         err64, state64 = l2_error_vs_exact(s, s.get_state(), t_fp64)
         cells64 = s.cells()
         s.close()
         del u_dev
-        sm_, u0m = build_problem(wl, "fp32", device)
-        sm_.set_state(torch.from_numpy(u0m).to(device))
-        del u0m
-        sm_.compute_dt()
-        t_m = torch.zeros(1, dtype=torch.float64, device=device)
-        run_steps(sm_, wl, args.warmup, t_m, 0)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        dofs_m = run_steps(sm_, wl, args.steps, t_m, args.warmup)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        el_m = f0.elapsed_time(f1) / 1e3
-        err32, state32 = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()))
-        same_mesh = np.array_equal(sm_.cells(), cells64)
-        t_pred32 = time_predictor(sm_, torch)
-        flops32 = predictor_flops_per_cell(sm_.dim, sm_.order, sm_.order + 1, sm_.nvar) * sm_.ncells
-        mixed = {"precision": "fp32 predictor contractions, fp64 state/faces/corrector",
-                 "value": dofs_m / el_m, "unit": "DoF-updates/s",
-                 "ms_per_step": el_m / args.steps * 1e3,
-                 "speedup_vs_fp64": (dofs_m / el_m) / value,
-                 "l2_rel_err_vs_exact": {"fp64": err64, "fp32": err32,
-                                         "vars": ["rho", "rho_u", "rho_v", "rho_w", "E"][:sm_.nvar]},
-                 "rel_l2_fp32_vs_fp64": (float(np.linalg.norm(state32 - state64) /
-                                               np.linalg.norm(state64)) if same_mesh else None),
-                 "max_abs_fp32_vs_fp64": (float(np.abs(state32 - state64).max())
-                                          if same_mesh else None),
-                 "predictor_launch_ms": t_pred32 * 1e3,
-                 "predictor_tflops": flops32 / t_pred32 / 1e12,
-                 "predictor_frac_of_fp32_peak": flops32 / t_pred32 / 1e12 / FP32_PEAK_TFLOPS}
-        del state64, state32
-        sm_.close()
+        mixed = {}
+        names = ["rho", "rho_u", "rho_v", "rho_w", "E"]
+        for prec in args.mixed.split(","):
+            if prec in ("tf32", "tf32x3", "bf16x3") and not (wl["dim"] == 3 and wl["order"] >= 5):
+                continue
+            sm_, u0m = build_problem(wl, prec, device)
+            sm_.set_state(torch.from_numpy(u0m).to(device))
+            sm_.compute_dt()
+            t_m = torch.zeros(1, dtype=torch.float64, device=device)
+            run_steps(sm_, wl, args.warmup, t_m, 0)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            dofs_m = run_steps(sm_, wl, args.steps, t_m, args.warmup)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            el_m = f0.elapsed_time(f1) / 1e3
+            err_m, state_m = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()))
+            same_mesh = np.array_equal(sm_.cells(), cells64)
+            per_var = None
+            if same_mesh:
+                per_var = {}
+                for v in range(sm_.nvar):
+                    dv = state_m[:, v] - state64[:, v]
+                    per_var[names[v]] = {
+                        "rel_l2": float(np.linalg.norm(dv) / np.linalg.norm(state64[:, v])),
+                        "max_abs": float(np.abs(dv).max())}
+            t_pred_m = time_predictor(sm_, torch)
+            flops_m = predictor_flops_per_cell(sm_.dim, sm_.order, sm_.order + 1,
+                                               sm_.nvar) * sm_.ncells
+            mixed[prec] = {
+                "value": dofs_m / el_m, "unit": "DoF-updates/s", "ms_per_step": el_m / args.steps * 1e3,
+                "speedup_vs_fp64": (dofs_m / el_m) / value,
+                "l2_rel_err_vs_exact": err_m, "vs_fp64_per_var": per_var,
+                "status": sm_.status(), "predictor_launch_ms": t_pred_m * 1e3,
+                "predictor_tflops": flops_m / t_pred_m / 1e12,
+                "predictor_frac_of_fp32_peak": flops_m / t_pred_m / 1e12 / FP32_PEAK_TFLOPS}
+            del state_m
+            sm_.close()
+        mixed["fp64_l2_rel_err_vs_exact"] = err64
+        mixed["vars"] = names[:len(err64)]
+        mixed["note"] = ("FP32 predictor arithmetic (CUDA cores or tensor cores), FP64 state, "
+                         "faces, Riemann, corrector and CFL reduction")
+        del state64
     else:
         s.close()
         del u_dev

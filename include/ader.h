@@ -61,10 +61,25 @@ typedef enum {
 
 typedef enum { ADER_EULER = 0, ADER_ACOUSTICS = 1 } ader_pde;
 
-/* Arithmetic of the predictor's contractions (Picard, time averages, face
- * extrapolation, volume term).  Riemann, restriction, corrector, CFL
- * reduction and the stored state are FP64 in every mode. */
-typedef enum { ADER_FP64 = 0, ADER_FP32 = 1 } ader_precision;
+/* Arithmetic of the predictor (Picard, time averages, face extrapolation,
+ * volume term).  Riemann, restriction, corrector, CFL reduction and the
+ * stored state are FP64 in every mode.
+ *   ADER_FP64    everything FP64
+ *   ADER_FP32    FP32 on the CUDA cores; FP64 zero-mean correction of the
+ *                volume term keeps the step conservative to FP64 rounding
+ *   ADER_TF32    as FP32, with the Picard derivative contractions on the tensor
+ *                cores (tcgen05, TF32 operands, FP32 accumulation in TMEM)
+ *   ADER_TF32X3  tensor cores with hi/lo TF32 splits (three products),
+ *                close to FP32 accuracy
+ *   ADER_BF16X3  tensor cores with hi/lo BF16 splits (three products)
+ * The tensor-core modes are available for 3D Euler at orders 5..7. */
+typedef enum {
+  ADER_FP64 = 0,
+  ADER_FP32 = 1,
+  ADER_TF32 = 2,
+  ADER_TF32X3 = 3,
+  ADER_BF16X3 = 4
+} ader_precision;
 
 typedef enum { ADER_ALL = 0, ADER_SKELETON = 1, ADER_ENCLAVE = 2 } ader_set;
 
@@ -177,7 +192,8 @@ ader_status ader_sphere_flags(ader_ctx* ctx, const double center[3], double radi
 
 /* Synchronise the context's streams and return the device status word
  * (bit 0 non-finite predictor, bit 1 non-physical state, bit 2 non-finite
- * CFL rate, bit 3 bad transfer index); clears it. */
+ * CFL rate, bit 3 bad transfer index, bit 4 a bounded wait for the tensor
+ * cores expired); clears it. */
 ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
 
 /* Discrete adjoint of one step: *lambda_out = A^T lambda_in, where A is the

@@ -60,9 +60,11 @@ ader_status cuda_fail(ader_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 cudaError_t do_predict(ader_ctx* c, const PredictArgs& a, cudaStream_t s) {
-  const Precision p = c->cfg.prec == ADER_FP32 ? Precision::kFP32 : Precision::kFP64;
+  const Precision p = static_cast<Precision>(int(c->cfg.prec));
   const int N = c->cfg.order;
   c->launches += a.count > 0 ? 1 : 0;
+  if (p == Precision::kTF32 || p == Precision::kTF32x3 || p == Precision::kBF16x3)
+    return predict_tc_euler3d(N, p, a, s);
   if (c->cfg.pde == ADER_EULER)
     return c->cfg.dim == 2 ? predict_euler2d(N, p, a, s) : predict_euler3d(N, p, a, s);
   return c->cfg.dim == 2 ? predict_acoustics2d(N, p, a, s) : predict_acoustics3d(N, p, a, s);
@@ -277,7 +279,9 @@ bool valid_config(const ader_config* cfg, std::string* why) {
   const int m = cfg->pde == ADER_EULER ? cfg->dim + 2 : cfg->dim + 1;
   if (cfg->nvar != m) return *why = "nvar does not match the pde", false;
   if (cfg->max_level < 0 || cfg->max_level > kMaxLevels - 2) return *why = "max_level out of range", false;
-  if (cfg->prec != ADER_FP64 && cfg->prec != ADER_FP32) return *why = "unknown precision", false;
+  if (cfg->prec < ADER_FP64 || cfg->prec > ADER_BF16X3) return *why = "unknown precision", false;
+  if (cfg->prec >= ADER_TF32 && !(cfg->dim == 3 && cfg->pde == ADER_EULER && cfg->order >= 5))
+    return *why = "tensor-core predictor: 3D Euler, order 5..7", false;
   if (!(cfg->cfl > 0.0)) return *why = "cfl must be positive", false;
   for (int d = 0; d < cfg->dim; ++d) {
     if (cfg->base[d] < 1) return *why = "base must be >= 1", false;

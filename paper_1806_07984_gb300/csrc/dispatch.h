@@ -15,5 +15,6 @@ ADER_DECLARE(euler3d)
 ADER_DECLARE(acoustics2d)
 ADER_DECLARE(acoustics3d)
 #undef ADER_DECLARE
+cudaError_t predict_tc_euler3d(int order, Precision p, const PredictArgs& a, cudaStream_t s);
 
 }  // namespace ader

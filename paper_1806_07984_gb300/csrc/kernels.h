@@ -23,6 +23,7 @@ enum StatusBits : uint32_t {
   kStatusNonPhysical = 2u,
   kStatusNonFiniteRate = 4u,
   kStatusBadTransfer = 8u,
+  kStatusTensorTimeout = 16u,
 };
 
 struct PredictArgs {
@@ -80,7 +81,7 @@ struct TransferArgs {
   BasisTables B;
 };
 
-enum class Precision { kFP64 = 0, kFP32 = 1 };
+enum class Precision { kFP64 = 0, kFP32 = 1, kTF32 = 2, kTF32x3 = 3, kBF16x3 = 4 };
 
 // Returns cudaErrorInvalidValue when (dim, order, pde, precision) has no
 // compiled kernel.

@@ -23,6 +23,7 @@
 
 #include "kernels.h"
 #include "pde.cuh"
+#include "tc.cuh"
 
 namespace ader {
 
@@ -48,11 +49,38 @@ struct PredictSmem {
   static constexpr int kPow2 = S::NS <= 1 ? 1 : (S::NS <= 2 ? 2 : (S::NS <= 4 ? 4 : (S::NS <= 8 ? 8 :
       (S::NS <= 16 ? 16 : (S::NS <= 32 ? 32 : (S::NS <= 64 ? 64 : (S::NS <= 128 ? 128 :
       (S::NS <= 256 ? 256 : 512))))))));
-  static constexpr size_t bytes() {
+  __host__ __device__ static constexpr size_t bytes() {
     return std::is_same<Real, double>::value
                ? size_t(kReal) * sizeof(Real)
                : size_t(kRedOffset) * 8 + size_t(S::CPB) * PDE::M * S::NS * 8;
   }
+};
+
+// Tensor-core modes of the derivative contractions (FP32 predictor only):
+// one TF32 product, three TF32 products of hi/lo splits (A_hi B_hi +
+// A_hi B_lo + A_lo B_hi), or three BF16 products of hi/lo splits.
+enum TcMode { kTcNone = 0, kTcTF32 = 1, kTcTF32x3 = 2, kTcBF16x3 = 3 };
+
+// Shared memory and TMEM of the tensor-core path (one cell per CTA, 3D):
+// per direction d the derivative along d of all m n^2 lines is the product
+// A_d[lines x K] B_d[N x K]^T with A_d the slice's fluxes f_d laid out line
+// by line (K = the coordinate along d, padded to 8 TF32 / 16 BF16 values) and
+// B_d = D / h_d padded to 16 x K; lines are cut into M = 128 tiles.
+template <int DIM, int N, class PDE, int TC>
+struct TcLayout {
+  static constexpr int n = N + 1;
+  static constexpr int ROWS = PDE::M * n * n;        // lines per direction
+  static constexpr int T = (ROWS + 127) / 128;       // M = 128 tiles per direction
+  static constexpr int NSPLIT = TC == kTcTF32 ? 1 : 2;
+  static constexpr int EB = TC == kTcBF16x3 ? 2 : 4; // operand element bytes
+  static constexpr int KIND = TC == kTcBF16x3 ? 1 : 0;
+  static constexpr int A_BYTES = NSPLIT * DIM * T * tc::kTileBytes;
+  static constexpr int B_BYTES = NSPLIT * DIM * 512;  // 16 rows x 32 bytes each
+  static constexpr int COLS_USED = DIM * T * 16;
+  static constexpr int COLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
+                              : COLS_USED <= 256 ? 256 : 512;
+  static constexpr int THREADS = (ipow(n, DIM) + 31) / 32 * 32;
+  __host__ __device__ static constexpr size_t bytes() { return size_t(A_BYTES + B_BYTES + 128); }
 };
 
 // One pass of the predictor over CPB cells of one CTA.  Thread t < CPB*NS
@@ -60,7 +88,7 @@ struct PredictSmem {
 // the barriers.  `cell` is the cell index (relative to the field pointers) of
 // this thread's cell and `valid` whether it exists; `ihd` its 1/h_d.  Every
 // thread of the CTA must call this with the same dt, B and iters.
-template <int DIM, int N, class PDE, class Real>
+template <int DIM, int N, class PDE, class Real, int TC = kTcNone>
 __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, double gamma_d,
                                               int iters, uint32_t* status, const double* u_in,
                                               double* ustar, double* faceQ, double* faceF,
@@ -125,8 +153,137 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       for (int j = 0; j < kDr; ++j) Dr[d][j] = sDh[cl][d][id[d] * n + j];
   }
 
+  // ---- tensor-core set-up: operand tiles, B = D/h_d splits, TMEM, mbarrier
+  using L = TcLayout<DIM, N, PDE, TC>;
+  static_assert(TC == kTcNone || (std::is_same<Real, float>::value && DIM == 3 && CPB == 1),
+                "tensor-core predictor: FP32, 3D, one cell per CTA");
+  __shared__ uint64_t tc_mbar;
+  __shared__ uint32_t tc_tmem;
+  uint8_t* tcA = nullptr;
+  uint8_t* tcB = nullptr;
+  uint32_t tc_phase = 0;
+  const int warp = tid >> 5, lane = tid & 31;
+  if constexpr (TC != kTcNone) {
+    // operand region after the predictor's own buffers, 128-byte aligned
+    uint8_t* base = smem_raw + PredictSmem<DIM, N, PDE, Real>::bytes();
+    const uint32_t sa = tc::smem_addr(base);
+    tcA = base + ((128u - (sa & 127u)) & 127u);
+    tcB = tcA + L::A_BYTES;
+    for (int i = tid; i < (L::A_BYTES + L::B_BYTES) / 4; i += blockDim.x)
+      reinterpret_cast<uint32_t*>(tcA)[i] = 0u;
+    __syncthreads();
+    // B_d[i][k] = D[i][k] / h_d for i, k < n (hi/lo split in the split modes)
+    for (int t = tid; t < DIM * n * n; t += blockDim.x) {
+      const int d = t / (n * n), i = (t / n) % n, k = t % n;
+      const double x = B.D[i][k] * ihd[d];
+      const uint32_t o = tc::canon(i, k * L::EB);
+      if constexpr (TC == kTcBF16x3) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(float(x));
+        const __nv_bfloat16 lo = __float2bfloat16_rn(float(x - double(__bfloat162float(hi))));
+        *reinterpret_cast<__nv_bfloat16*>(tcB + d * 512 + o) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(tcB + (DIM + d) * 512 + o) = lo;
+      } else {
+        const float hi = tc::to_tf32(float(x));
+        *reinterpret_cast<float*>(tcB + d * 512 + o) = TC == kTcTF32 ? float(x) : hi;
+        if (TC == kTcTF32x3) *reinterpret_cast<float*>(tcB + (DIM + d) * 512 + o) = float(x - double(hi));
+      }
+    }
+    if (warp == 0) tc::alloc(&tc_tmem, L::COLS);
+    if (tid == 0) tc::mbar_init(&tc_mbar, 1);
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+
   // g = sum_d (D/h_d)^(d) f_d(x) at this node, for the slice held in x.
   auto divergence = [&](const Real(&x)[M], Real(&g)[M]) {
+    if constexpr (TC != kTcNone) {
+      Real f[DIM][M];
+      PDE::fluxes(x, f, gamma);
+      if (active) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          // line index of this node across direction d (lowest tangential first)
+          const int tl = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            const int r = v * n * n + tl;
+            const uint32_t o = (d * L::T + (r >> 7)) * tc::kTileBytes + tc::canon(r & 127, id[d] * L::EB);
+            const float val = float(f[d][v]);
+            if constexpr (TC == kTcBF16x3) {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+              *reinterpret_cast<__nv_bfloat16*>(tcA + o) = hi;
+              *reinterpret_cast<__nv_bfloat16*>(tcA + DIM * L::T * tc::kTileBytes + o) =
+                  __float2bfloat16_rn(val - __bfloat162float(hi));
+            } else if constexpr (TC == kTcTF32x3) {
+              const float hi = tc::to_tf32(val);
+              *reinterpret_cast<float*>(tcA + o) = hi;
+              *reinterpret_cast<float*>(tcA + DIM * L::T * tc::kTileBytes + o) = val - hi;
+            } else {
+              *reinterpret_cast<float*>(tcA + o) = tc::to_tf32(val);
+            }
+          }
+        }
+      }
+      tc::fence_proxy_async();
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      const uint32_t taddr = tc_tmem;
+      if (tid == 0) {
+        constexpr uint32_t ID = tc::idesc(L::KIND == 0 ? 2u : 1u, 128, 16);
+        const uint32_t a0 = tc::smem_addr(tcA), b0 = tc::smem_addr(tcB);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+          for (int t = 0; t < L::T; ++t) {
+            const uint32_t dst = taddr + uint32_t((d * L::T + t) * 16);
+            const uint32_t ahi = a0 + (d * L::T + t) * tc::kTileBytes;
+            const uint32_t bhi = b0 + d * 512;
+            tc::mma<L::KIND>(dst, tc::sdesc(ahi), tc::sdesc(bhi), ID, false);
+            if constexpr (L::NSPLIT == 2) {
+              const uint32_t alo = ahi + DIM * L::T * tc::kTileBytes;
+              const uint32_t blo = bhi + DIM * 512;
+              tc::mma<L::KIND>(dst, tc::sdesc(ahi), tc::sdesc(blo), ID, true);
+              tc::mma<L::KIND>(dst, tc::sdesc(alo), tc::sdesc(bhi), ID, true);
+            }
+          }
+        tc::commit(&tc_mbar);
+      }
+      if (!tc::mbar_wait(&tc_mbar, tc_phase, 1 << 22)) atomicOr(status, kStatusTensorTimeout);
+      tc_phase ^= 1u;
+      tc::fence_after();
+      // read the accumulators back: warp w serves lane quarter w % 4
+      Real* G = my_fb;  // [DIM][M][NS]: derivative along d of f_d, per node
+      const int q = warp & 3;
+      const int nwq = (int(blockDim.x >> 5) - q + 3) >> 2;
+      for (int job = warp >> 2; job < DIM * L::T; job += nwq) {
+        const int d = job / L::T, t = job % L::T;
+        float vals[8];
+        tc::ld8(taddr + uint32_t((d * L::T + t) * 16) + (uint32_t(q * 32) << 16), vals);
+        const int r = t * 128 + q * 32 + lane;
+        if (r < L::ROWS) {
+          const int v = r / (n * n), tl = r % (n * n);
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            const int nd = d == 0 ? i + n * tl
+                                  : (d == 1 ? (tl % n) + n * i + n * n * (tl / n) : tl + n * n * i);
+            G[(d * M + v) * NS + nd] = vals[i];
+          }
+        }
+      }
+      tc::fence_before();
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        g[v] = Real(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) g[v] += active ? G[(d * M + v) * NS + node] : Real(0);
+      }
+      __syncthreads();
+      return;
+    }
     Real f[DIM][M];
     PDE::fluxes(x, f, gamma);
     if (active) {
@@ -269,6 +426,11 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
     for (int v = 0; v < M; ++v) vol[v] -= my_red[v * NS];
   }
+  if constexpr (TC != kTcNone) {
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tc_tmem, L::COLS);
+  }
   if (!valid) return;
 #pragma unroll
   for (int v = 0; v < M; ++v) {
@@ -323,6 +485,38 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
   for (int d = 0; d < DIM; ++d) ihd[d] = a.inv_h[lv][d];
   predict_cells<DIM, N, PDE, Real>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u, a.ustar, a.faceQ,
                                    a.faceF, cell, valid, ihd, smem_raw);
+}
+
+// Tensor-core predictor: one CTA (whole warps) per cell.
+template <int N, class PDE, int TC>
+__global__ void __launch_bounds__(TcLayout<3, N, PDE, TC>::THREADS)
+    predict_tc_kernel(const PredictArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t slot = blockIdx.x;
+  const bool valid = slot < a.count;
+  const int64_t cell = valid ? int64_t(a.cells[slot]) : 0;
+  double ihd[3];
+  const int lv = valid ? int(a.level[cell]) : 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ihd[d] = a.inv_h[lv][d];
+  predict_cells<3, N, PDE, float, TC>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u, a.ustar,
+                                      a.faceQ, a.faceF, cell, valid, ihd, smem_raw);
+}
+
+template <int N, class PDE, int TC>
+cudaError_t launch_predict_tc_t(const PredictArgs& a, cudaStream_t s) {
+  using L = TcLayout<3, N, PDE, TC>;
+  if (a.count == 0) return cudaSuccess;
+  const size_t smem = PredictSmem<3, N, PDE, float>::bytes() + L::bytes();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(predict_tc_kernel<N, PDE, TC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  predict_tc_kernel<N, PDE, TC><<<dim3(unsigned(a.count)), dim3(L::THREADS), smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int DIM, int N, class PDE, class Real>

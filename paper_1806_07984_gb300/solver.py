@@ -32,7 +32,7 @@ class Solver:
             cfg.hi[d] = hi[d] if d < dim else 1.0
         cfg.max_level = max_level
         cfg.picard_iters = picard_iters
-        cfg.prec = A.ADER_FP64 if precision == "fp64" else A.ADER_FP32
+        cfg.prec = A.PRECISIONS[precision]
         self.cfg = cfg
         self.dim, self.order, self.n, self.nvar = dim, order, order + 1, cfg.nvar
         with torch.cuda.device(self.device):

@@ -152,3 +152,15 @@ def test_nonphysical_state_sets_status():
     solver.step(1)
     assert solver.status() & 2
     assert solver.status() == 0   # reading clears it
+
+
+# Tensor-core predictor (tcgen05): stated bounds on the state after one step
+# against the FP64 oracle -- 3xTF32 and 3xBF16 splits at the FP32 bar, plain
+# TF32 at 1e-4 (its operands carry 11 significant bits).
+@pytest.mark.parametrize("order,precision,tol", [
+    (5, "tf32x3", TOL32), (5, "bf16x3", TOL32), (5, "tf32", 1e-4),
+    (7, "tf32x3", TOL32), (7, "bf16x3", TOL32), (7, "tf32", 1e-4), (6, "tf32x3", TOL32)])
+def test_tensor_core_predictor_bound(order, precision, tol):
+    base, lvl = (3, 1) if order == 5 else (2, 0)
+    stage_parity(3, order, "euler", base, lvl, [(0.5, 0.5, 0.5)] * lvl, 0.2, seed=60 + order,
+                 tol=tol, precision=precision)
