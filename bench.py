@@ -269,14 +269,15 @@ def run_batched(torch, precision, steps, warmup, count=512):
                                                    "step_ms": tune_ms}, "status": status}
 
 
-def run_adjoint(torch):
-    """3D linear acoustics N=4 on 27^3 (Picard 13 iterations, FP64): one loss
-    and gradient with respect to the initial state over 50 steps, 64 receivers,
-    checkpoints every 10 steps (forward + recomputation + adjoint sweep)."""
+def run_adjoint(torch, predictor="picard"):
+    """3D linear acoustics N=4 on 27^3 (FP64; Picard with 13 iterations or the
+    Cauchy-Kowalevski predictor): one loss and gradient with respect to the
+    initial state over 50 steps, 64 receivers, checkpoints every 10 steps
+    (forward + recomputation + adjoint sweep)."""
     from paper_1806_07984_gb300 import Solver, adjoint as adj, ader as A
     order = 4
     s = Solver(3, order, "acoustics", base=(27, 27, 27), cfl=workloads.ADER_CFL[order],
-               picard_iters=3 * order + 1)
+               picard_iters=3 * order + 1, predictor=predictor)
     X = s.node_coords()
     u0 = torch.from_numpy(np.ascontiguousarray(
         np.moveaxis(workloads.acoustic_pulses(X, seed=1), 0, 1))).cuda()
@@ -316,7 +317,7 @@ def run_adjoint(torch):
     dofs = s.ncells * s.nvar * s.n ** 3
     s.close()
     return {"workload": "3D acoustics N=4, 27^3 periodic, 50 steps, 64 receivers, checkpoints every 10",
-            "loss": float(loss), "grad_norm": float(u.grad.norm()),
+            "predictor": predictor, "loss": float(loss.detach()), "grad_norm": float(u.grad.norm()),
             "forward_s": t_fwd, "backward_s": t_bwd, "gradient_s": t_fwd + t_bwd,
             "adjoint_step_ms": t_adj * 1e3, "adjoint_dof_updates_per_s": dofs / t_adj,
             "dofs": dofs}
@@ -558,7 +559,8 @@ def main():
         batched = {"fp64": run_batched(torch, "fp64", 20, 2),
                    "fp32": run_batched(torch, "fp32", 20, 2)}
 
-    adjoint = run_adjoint(torch) if (not args.no_adjoint and world == 1) else None
+    adjoint = ({"picard": run_adjoint(torch, "picard"), "ck": run_adjoint(torch, "ck")}
+               if (not args.no_adjoint and world == 1) else None)
 
     # ---- end to end through the public API with host buffers ---------------
     # Every step: H2D of the state from pinned host memory, one step, D2H of

@@ -83,6 +83,12 @@ typedef enum {
 
 typedef enum { ADER_ALL = 0, ADER_SKELETON = 1, ADER_ENCLAVE = 2 } ader_set;
 
+/* Space-time predictor: Picard iteration (Sec. 2.1; any PDE) or, for the
+ * linear acoustics PDE, the Cauchy-Kowalevski Taylor expansion in time
+ * (Sec. 2.4): d_0 = u, d_{k+1} = -sum_d D^(d) f_d(d_k) / h_d, time average
+ * sum_{k<=N} dt^k / (k+1)! d_k. */
+typedef enum { ADER_PREDICTOR_PICARD = 0, ADER_PREDICTOR_CK = 1 } ader_predictor;
+
 typedef enum {
   ADER_FIELD_U = 0,       /* u(T) or u(T+dt) after ader_correct        [c][var][node] */
   ADER_FIELD_USTAR = 1,   /* u + dt * volume term (ader_predict)       [c][var][node] */
@@ -104,6 +110,7 @@ typedef struct {
   int max_level;     /* refinement levels above the base grid, 0..6 */
   int picard_iters;  /* Picard iterations; 0 selects order + 1 */
   ader_precision prec;
+  ader_predictor predictor;  /* ADER_PREDICTOR_CK: acoustics, FP64 or FP32 */
 } ader_config;
 
 typedef struct ader_ctx ader_ctx;
@@ -202,7 +209,8 @@ ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
  * dt_dev.  Each task of Eq. (4) is transposed in reverse order (corrector
  * lifting, Rusanov with s = c = 1, predictor volume term and face
  * extrapolation, time averages, and the Picard iterations unrolled with the
- * forward count).  Needs a mesh without resolution transitions; lambda
+ * forward count, or the Cauchy-Kowalevski sum transposed by Horner's
+ * scheme).  FP64 only.  Needs a mesh without resolution transitions; lambda
  * arrays are device [c][var][node] and must not alias.  Uses the context's
  * face buffers as scratch. */
 ader_status ader_adjoint_step(ader_ctx* ctx, const double* lambda_in, double* lambda_out,

@@ -24,9 +24,14 @@ class StepOutput:
     dt_next: float
 
 
-def predict(u, h, dt, pde, B, iters):
-    """C_STP followed by id|T+dT and id|dc, plus the corrector's volume term."""
-    q = ader.picard_predictor(u, h, dt, pde, B, iters)
+def predict(u, h, dt, pde, B, iters, predictor="picard"):
+    """C_STP followed by id|T+dT and id|dc, plus the corrector's volume term.
+    ``predictor`` selects Picard iteration or, for a linear PDE, the
+    Cauchy-Kowalevski Taylor expansion (Sec. 2.4)."""
+    if predictor == "ck":
+        q = ader.ck_predictor(u, h, dt, pde, B)
+    else:
+        q = ader.picard_predictor(u, h, dt, pde, B, iters)
     qbar, fbar = ader.time_average(q, pde, B)
     ustar = ader.volume_update(u, fbar, h, dt, B)
     Qf, Ff = ader.project_to_faces(qbar, fbar, B)
@@ -78,11 +83,11 @@ def correct(ustar, Fs, h, dt, pde, B):
     return u, ader.cfl_dt(u, h, pde, B.order)
 
 
-def step(mesh, u, dt, pde, B, iters=None):
+def step(mesh, u, dt, pde, B, iters=None, predictor="picard"):
     if iters is None:
         iters = B.order + 1
     h = mesh.cell_widths()
-    ustar, Qf, Ff = predict(u, h, dt, pde, B, iters)
+    ustar, Qf, Ff = predict(u, h, dt, pde, B, iters, predictor)
     Fs = riemann(mesh, Qf, Ff, pde, B)
     unew, dt_next = correct(ustar, Fs, h, dt, pde, B)
     return StepOutput(unew, ustar, Qf, Ff, Fs, dt_next)

@@ -23,6 +23,7 @@ ADER_FP64, ADER_FP32, ADER_TF32, ADER_TF32X3, ADER_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": ADER_FP64, "fp32": ADER_FP32, "tf32": ADER_TF32, "tf32x3": ADER_TF32X3,
               "bf16x3": ADER_BF16X3}
 ADER_ALL, ADER_SKELETON, ADER_ENCLAVE = 0, 1, 2
+ADER_PREDICTOR_PICARD, ADER_PREDICTOR_CK = 0, 1
 ADER_FIELD_U, ADER_FIELD_USTAR, ADER_FIELD_FACE_Q, ADER_FIELD_FACE_F, ADER_FIELD_FSTAR = range(5)
 
 # Every symbol the header declares (checked by the CPU test suite).
@@ -57,7 +58,7 @@ class ader_config(ctypes.Structure):
                 ("pde", ctypes.c_int), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("base", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("max_level", ctypes.c_int),
-                ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int)]
+                ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int), ("predictor", ctypes.c_int)]
 
 
 _lib = None

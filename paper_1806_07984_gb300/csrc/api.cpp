@@ -65,6 +65,8 @@ cudaError_t do_predict(ader_ctx* c, const PredictArgs& a, cudaStream_t s) {
   c->launches += a.count > 0 ? 1 : 0;
   if (p == Precision::kTF32 || p == Precision::kTF32x3 || p == Precision::kBF16x3)
     return predict_tc_euler3d(N, p, a, s);
+  if (c->cfg.predictor == ADER_PREDICTOR_CK)
+    return c->cfg.dim == 2 ? predict_ck_acoustics2d(N, p, a, s) : predict_ck_acoustics3d(N, p, a, s);
   if (c->cfg.pde == ADER_EULER)
     return c->cfg.dim == 2 ? predict_euler2d(N, p, a, s) : predict_euler3d(N, p, a, s);
   return c->cfg.dim == 2 ? predict_acoustics2d(N, p, a, s) : predict_acoustics3d(N, p, a, s);
@@ -291,6 +293,10 @@ bool valid_config(const ader_config* cfg, std::string* why) {
     if (cells >= (1 << 20)) return *why = "grid too fine for the cell key", false;
   }
   if (cfg->picard_iters < 0) return *why = "picard_iters must be >= 0", false;
+  if (cfg->predictor != ADER_PREDICTOR_PICARD && cfg->predictor != ADER_PREDICTOR_CK)
+    return *why = "unknown predictor", false;
+  if (cfg->predictor == ADER_PREDICTOR_CK && (cfg->pde != ADER_ACOUSTICS || cfg->prec > ADER_FP32))
+    return *why = "Cauchy-Kowalevski predictor: linear acoustics, FP64 or FP32", false;
   return true;
 }
 
@@ -582,8 +588,8 @@ ader_status ader_status_word(ader_ctx* c, uint32_t* out) {
 ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out,
                               const double* dt_dev, void* stream) {
   if (!c || !lam_in || !lam_out || !dt_dev || lam_in == lam_out) return ADER_ERR_ARG;
-  if (c->cfg.pde != ADER_ACOUSTICS) {
-    c->err = "the adjoint step is implemented for linear acoustics";
+  if (c->cfg.pde != ADER_ACOUSTICS || c->cfg.prec != ADER_FP64) {
+    c->err = "the adjoint step is implemented for linear acoustics in FP64";
     return ADER_ERR_ARG;
   }
   if (!c->tree.parents.empty()) {
@@ -602,6 +608,7 @@ ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out
   a.ncells = int64_t(c->tree.cells.size());
   a.dt = dt_dev;
   a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
+  a.scheme = c->cfg.predictor;
   std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
   a.B = c->B;
   c->launches += 3;

@@ -15,6 +15,8 @@ ADER_DECLARE(euler3d)
 ADER_DECLARE(acoustics2d)
 ADER_DECLARE(acoustics3d)
 #undef ADER_DECLARE
+cudaError_t predict_ck_acoustics2d(int order, Precision prec, const PredictArgs& a, cudaStream_t s);
+cudaError_t predict_ck_acoustics3d(int order, Precision prec, const PredictArgs& a, cudaStream_t s);
 cudaError_t predict_tc_euler3d(int order, Precision p, const PredictArgs& a, cudaStream_t s);
 
 }  // namespace ader

@@ -47,3 +47,14 @@ cudaError_t with_order(int order, F&& f) {
                       [&](auto N) { return launch_transfer_t<DIM, N.value, PDE::M>(a, s); });  \
   }                                                                                            \
   }
+
+// Cauchy-Kowalevski predictor (linear PDEs only).
+#define ADER_INSTANTIATE_CK(TAG, DIM, PDE)                                                       \
+  namespace ader {                                                                               \
+  cudaError_t predict_ck_##TAG(int order, Precision prec, const PredictArgs& a, cudaStream_t s) { \
+    return with_order(order, [&](auto N) {                                                       \
+      return prec == Precision::kFP64 ? launch_predict_t<DIM, N.value, PDE, double, 1>(a, s)     \
+                                      : launch_predict_t<DIM, N.value, PDE, float, 1>(a, s);     \
+    });                                                                                          \
+  }                                                                                              \
+  }

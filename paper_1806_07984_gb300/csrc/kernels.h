@@ -108,6 +108,7 @@ struct AdjointArgs {
   int64_t ncells;
   const double* dt;
   int iters;
+  int scheme;  // 0 Picard, 1 Cauchy-Kowalevski
   double inv_h[kMaxLevels][3];
   BasisTables B;
 };

@@ -88,7 +88,7 @@ struct TcLayout {
 // the barriers.  `cell` is the cell index (relative to the field pointers) of
 // this thread's cell and `valid` whether it exists; `ihd` its 1/h_d.  Every
 // thread of the CTA must call this with the same dt, B and iters.
-template <int DIM, int N, class PDE, class Real, int TC = kTcNone>
+template <int DIM, int N, class PDE, class Real, int TC = kTcNone, int SCHEME = 0>
 __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, double gamma_d,
                                               int iters, uint32_t* status, const double* u_in,
                                               double* ustar, double* faceQ, double* faceF,
@@ -315,59 +315,83 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     __syncthreads();
   };
 
-  // First Picard iteration: the initial guess u is constant in time, so one
-  // slice gives every time node: q_k = u - dt (sum_l Mt[k][l]) g(u).
-  Real q[n][M];
-  {
-    Real g[M];
-    divergence(uu, g);
+  Real qb[M], Fb[DIM][M];
+  if constexpr (SCHEME == 1) {
+    // Cauchy-Kowalevski (linear PDEs, Sec. 2.4): d_0 = u, d_{k+1} = -sum_d
+    // (D/h_d)^(d) f_d(d_k); the time average of the Taylor polynomial is
+    // Q-bar = sum_k dt^k / (k+1)! d_k and F-bar_d = f_d(Q-bar).
+    Real dk[M];
 #pragma unroll
-    for (int k = 0; k < n; ++k)
+    for (int v = 0; v < M; ++v) {
+      dk[v] = uu[v];
+      qb[v] = uu[v];
+    }
+    Real c = Real(1);
 #pragma unroll
-      for (int v = 0; v < M; ++v) q[k][v] = fma(sRs[k], g[v], uu[v]);
-  }
-  for (int r = 1; r < iters; ++r) {
-    Real acc[n][M];
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int v = 0; v < M; ++v) acc[k][v] = uu[v];
-#pragma unroll
-    for (int l = 0; l < n; ++l) {
+    for (int k = 1; k <= N; ++k) {
       Real g[M];
-      divergence(q[l], g);
+      divergence(dk, g);
+      c = c * Real(dt) / Real(k + 1);
 #pragma unroll
-      for (int k = 0; k < n; ++k) {
-        const Real c = sMd[k * n + l];
-#pragma unroll
-        for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
+      for (int v = 0; v < M; ++v) {
+        dk[v] = -g[v];
+        qb[v] = fma(c, dk[v], qb[v]);
       }
     }
+    PDE::fluxes(qb, Fb, gamma);
+  } else {
+    // First Picard iteration: the initial guess u is constant in time, so one
+    // slice gives every time node: q_k = u - dt (sum_l Mt[k][l]) g(u).
+    Real q[n][M];
+    {
+      Real g[M];
+      divergence(uu, g);
 #pragma unroll
-    for (int k = 0; k < n; ++k)
+      for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int v = 0; v < M; ++v) q[k][v] = acc[k][v];
-  }
-
-  // Time averages of the final iterate and of its fluxes.
-  Real qb[M], Fb[DIM][M];
+        for (int v = 0; v < M; ++v) q[k][v] = fma(sRs[k], g[v], uu[v]);
+    }
+    for (int r = 1; r < iters; ++r) {
+      Real acc[n][M];
 #pragma unroll
-  for (int v = 0; v < M; ++v) qb[v] = Real(0);
+      for (int k = 0; k < n; ++k)
 #pragma unroll
-  for (int d = 0; d < DIM; ++d)
+        for (int v = 0; v < M; ++v) acc[k][v] = uu[v];
 #pragma unroll
-    for (int v = 0; v < M; ++v) Fb[d][v] = Real(0);
+      for (int l = 0; l < n; ++l) {
+        Real g[M];
+        divergence(q[l], g);
 #pragma unroll
-  for (int k = 0; k < n; ++k) {
-    Real f[DIM][M];
-    PDE::fluxes(q[k], f, gamma);
-    const Real wk = sw[k];
+        for (int k = 0; k < n; ++k) {
+          const Real c = sMd[k * n + l];
 #pragma unroll
-    for (int v = 0; v < M; ++v) qb[v] = fma(wk, q[k][v], qb[v]);
+          for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int v = 0; v < M; ++v) q[k][v] = acc[k][v];
+    }
+    // Time averages of the final iterate and of its fluxes.
+#pragma unroll
+    for (int v = 0; v < M; ++v) qb[v] = Real(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int v = 0; v < M; ++v) Fb[d][v] = fma(wk, f[d][v], Fb[d][v]);
+      for (int v = 0; v < M; ++v) Fb[d][v] = Real(0);
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      Real f[DIM][M];
+      PDE::fluxes(q[k], f, gamma);
+      const Real wk = sw[k];
+#pragma unroll
+      for (int v = 0; v < M; ++v) qb[v] = fma(wk, q[k][v], qb[v]);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+#pragma unroll
+        for (int v = 0; v < M; ++v) Fb[d][v] = fma(wk, f[d][v], Fb[d][v]);
+    }
   }
   bool finite = true;
 #pragma unroll
@@ -470,7 +494,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   }
 }
 
-template <int DIM, int N, class PDE, class Real>
+template <int DIM, int N, class PDE, class Real, int SCHEME = 0>
 __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
     predict_kernel(const PredictArgs a) {
   using S = PredictShape<DIM, N>;
@@ -483,8 +507,9 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
   const int lv = valid ? int(a.level[cell]) : 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) ihd[d] = a.inv_h[lv][d];
-  predict_cells<DIM, N, PDE, Real>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u, a.ustar, a.faceQ,
-                                   a.faceF, cell, valid, ihd, smem_raw);
+  predict_cells<DIM, N, PDE, Real, kTcNone, SCHEME>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u,
+                                                    a.ustar, a.faceQ, a.faceF, cell, valid, ihd,
+                                                    smem_raw);
 }
 
 // Tensor-core predictor: one CTA (whole warps) per cell.
@@ -519,20 +544,20 @@ cudaError_t launch_predict_tc_t(const PredictArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int DIM, int N, class PDE, class Real>
+template <int DIM, int N, class PDE, class Real, int SCHEME = 0>
 cudaError_t launch_predict_t(const PredictArgs& a, cudaStream_t s) {
   using S = PredictShape<DIM, N>;
   if (a.count == 0) return cudaSuccess;
   const size_t smem = PredictSmem<DIM, N, PDE, Real>::bytes();
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(predict_kernel<DIM, N, PDE, Real>,
+    cudaError_t e = cudaFuncSetAttribute(predict_kernel<DIM, N, PDE, Real, SCHEME>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const int64_t blocks = (a.count + S::CPB - 1) / S::CPB;
-  predict_kernel<DIM, N, PDE, Real><<<dim3(unsigned(blocks)), dim3(S::THREADS), smem, s>>>(a);
+  predict_kernel<DIM, N, PDE, Real, SCHEME><<<dim3(unsigned(blocks)), dim3(S::THREADS), smem, s>>>(a);
   return cudaGetLastError();
 }
 

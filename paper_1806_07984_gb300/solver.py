@@ -15,7 +15,7 @@ class Solver:
 
     def __init__(self, dim, order, pde="euler", base=(27, 27, 27), max_level=0, cfl=0.1,
                  gamma=1.4, picard_iters=0, precision="fp64", lo=(0.0, 0.0, 0.0),
-                 hi=(1.0, 1.0, 1.0), device=None):
+                 hi=(1.0, 1.0, 1.0), device=None, predictor="picard"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda" if device is None else device)
@@ -33,6 +33,7 @@ class Solver:
         cfg.max_level = max_level
         cfg.picard_iters = picard_iters
         cfg.prec = A.PRECISIONS[precision]
+        cfg.predictor = A.ADER_PREDICTOR_CK if predictor == "ck" else A.ADER_PREDICTOR_PICARD
         self.cfg = cfg
         self.dim, self.order, self.n, self.nvar = dim, order, order + 1, cfg.nvar
         with torch.cuda.device(self.device):

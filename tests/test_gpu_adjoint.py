@@ -11,18 +11,19 @@ from gpu_helpers import lib_keys, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def solver_for(dim, order, base, iters):
+def solver_for(dim, order, base, iters, predictor="picard"):
     from paper_1806_07984_gb300 import Solver
     return Solver(dim, order, "acoustics", base=(base,) * 3, max_level=0,
-                  cfl=workloads.ADER_CFL[order], picard_iters=iters)
+                  cfl=workloads.ADER_CFL[order], picard_iters=iters, predictor=predictor)
 
 
-@pytest.mark.parametrize("dim,order,base", [(3, 2, 2), (2, 3, 3)])
-def test_adjoint_equals_transpose_of_oracle_step(dim, order, base):
+@pytest.mark.parametrize("dim,order,base,predictor", [(3, 2, 2, "picard"), (2, 3, 3, "picard"),
+                                                      (3, 2, 2, "ck"), (2, 4, 3, "ck")])
+def test_adjoint_equals_transpose_of_oracle_step(dim, order, base, predictor):
     import torch
     from paper_1806_07984_gb300 import ader as A
     iters = dim * order + 1
-    s = solver_for(dim, order, base, iters)
+    s = solver_for(dim, order, base, iters, predictor)
     m = omesh.Mesh(dim, (base,) * dim, 0)
     perm = np.array([m.index[k] for k in lib_keys(s)])
     B = obasis.Basis(order)
@@ -34,7 +35,8 @@ def test_adjoint_equals_transpose_of_oracle_step(dim, order, base):
     for j in range(size):
         e = np.zeros(size)
         e[j] = 1.0
-        Amat[:, j] = ostep.step(m, e.reshape(shape), dt, P, B, iters=iters).u.ravel()
+        Amat[:, j] = ostep.step(m, e.reshape(shape), dt, P, B, iters=iters,
+                                predictor=predictor).u.ravel()
     rng = np.random.default_rng(1)
     y = rng.standard_normal(shape)
     ref = (Amat.T @ y.ravel()).reshape(shape)          # oracle order
@@ -111,3 +113,33 @@ def test_misfit_gradient_vs_central_differences(cfg5):
         fd = (lp - lm) / (2 * h)
         an = float((grad * v).sum())
         assert abs(fd - an) <= 1e-5 * abs(an), (k, fd, an)
+
+
+def test_ck_gradient_vs_central_differences():
+    """The misfit gradient with the Cauchy-Kowalevski predictor (27^3, N=4)."""
+    import torch
+    from paper_1806_07984_gb300 import adjoint as adj
+    s = solver_for(3, 4, 27, 0, "ck")
+    X = s.node_coords()
+    u0 = torch.from_numpy(np.ascontiguousarray(
+        np.moveaxis(workloads.acoustic_pulses(X, seed=1), 0, 1))).cuda()
+    uobs = torch.from_numpy(np.ascontiguousarray(
+        np.moveaxis(workloads.acoustic_pulses(X, seed=3), 0, 1))).cuda()
+    s.set_state(u0)
+    s.compute_dt()
+    dt = s.dt.clone()
+    rec = adj.Receivers(s, workloads.acoustic_receivers(64, seed=2))
+    nsteps = 50
+    p_obs, _ = adj.forward_run(s, uobs, dt, rec, nsteps)
+    loss_fn = adj.AcousticMisfit.make(s, dt, rec, p_obs, nsteps, every=10)
+    u = u0.clone().requires_grad_(True)
+    loss_fn(u).backward()
+    g = torch.Generator(device="cuda").manual_seed(8)
+    for k in range(4):
+        v = torch.randn(u0.shape, dtype=torch.float64, device="cuda", generator=g)
+        lp, _ = adj.misfit(s, u0 + 1e-6 * v, dt, rec, p_obs, nsteps)
+        lm, _ = adj.misfit(s, u0 - 1e-6 * v, dt, rec, p_obs, nsteps)
+        fd = (lp - lm) / 2e-6
+        an = float((u.grad * v).sum())
+        assert abs(fd - an) <= 1e-5 * abs(an), (k, fd, an)
+    s.close()

@@ -16,16 +16,16 @@ TOL32 = 1e-6
 
 
 def stage_parity(dim, order, pde, base, max_level, centers, radius, seed, tol=TOL64,
-                 precision="fp64"):
+                 precision="fp64", predictor="picard"):
     import paper_1806_07984_gb300.ader as A
     solver, om, perm = build_pair(dim, order, pde, base, max_level, centers, radius,
-                                  precision=precision)
+                                  precision=precision, predictor=predictor)
     B = obasis.Basis(order)
     P = opde.make_pde(pde, dim)
     u0 = random_state(om, B, pde, seed)
     h = om.cell_widths()
     dt = oader.cfl_dt(u0, h, P, order, cfl=workloads.ADER_CFL[order])
-    ref = ostep.step(om, u0, dt, P, B)
+    ref = ostep.step(om, u0, dt, P, B, predictor=predictor)
     solver.set_state(u0[perm])
     solver.set_dt(dt)
     solver.predict()
@@ -169,3 +169,13 @@ def test_tensor_core_predictor_bound(order, precision, tol):
     base, lvl = (3, 1) if order == 5 else (2, 0)
     stage_parity(3, order, "euler", base, lvl, [(0.5, 0.5, 0.5)] * lvl, 0.2, seed=60 + order,
                  tol=tol, precision=precision)
+
+
+@pytest.mark.parametrize("dim,order,precision,tol", [(2, 3, "fp64", TOL64), (3, 4, "fp64", TOL64),
+                                                     (3, 7, "fp64", TOL64), (3, 4, "fp32", TOL32)])
+def test_cauchy_kowalevski_predictor(dim, order, precision, tol):
+    """Linear acoustics with the Cauchy-Kowalevski predictor on AMR meshes."""
+    c = (0.45, 0.5, 0.55)[:dim]
+    base, lvl = (9, 2) if dim == 2 else ((3, 2) if order < 7 else (2, 0))
+    stage_parity(dim, order, "acoustics", base, lvl, [c] * lvl, 0.12, seed=70 + order, tol=tol,
+                 precision=precision, predictor="ck")

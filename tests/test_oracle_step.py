@@ -200,3 +200,23 @@ def test_step_sample_equals_full_step(which, N, request):
                               rng.choice(len(m.cells), 6, replace=False)])
     got = stepmod.step_sample(m, u, dt, P, B, targets)
     assert np.abs(got - full.u[targets]).max() < 1e-13
+
+
+def test_ck_step_conserves_and_matches_picard_on_1d_data(amr2d):
+    """The Cauchy-Kowalevski step conserves on an AMR mesh; on data varying
+    along x only (uniform mesh) it equals the Picard step (both predictors are
+    the exact local evolution there)."""
+    B = basis.Basis(3)
+    P = pdes.Acoustics(2)
+    u = random_state(amr2d, B, "acoustics", seed=4)
+    h = amr2d.cell_widths()
+    dt = ader.cfl_dt(u, h, P, 3)
+    out = stepmod.step(amr2d, u, dt, P, B, predictor="ck")
+    assert np.allclose(ader.cell_integral(out.u, h, B), ader.cell_integral(u, h, B), atol=1e-13)
+    m = meshmod.Mesh(2, (9, 9), 0)
+    X = m.node_coords(B.xi)
+    u1 = np.stack([np.sin(2 * np.pi * X[0]), np.cos(2 * np.pi * X[0]), 0 * X[0]], axis=1)
+    dt = ader.cfl_dt(u1, m.cell_widths(), P, 3)
+    a = stepmod.step(m, u1, dt, P, B, iters=4, predictor="ck").u
+    b = stepmod.step(m, u1, dt, P, B, iters=4).u
+    assert np.abs(a - b).max() < 1e-13
