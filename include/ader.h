@@ -188,6 +188,16 @@ ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
  * into children, L2 projection onto parents).  Synchronises the device. */
 ader_status ader_remesh(ader_ctx* ctx, const int8_t* flags);
 
+/* Solution-based criterion (Sec. 2.4: first derivatives of the solution),
+ * the AMR epilogue of the corrector: eta[c] = max over the nodes of
+ * h_c |grad u_var| with h_c = max_d h_d, computed on the device from the
+ * current state; flags[c] = +1 if eta > refine_above and the cell is below
+ * max_level, -1 if eta < coarsen_below and the cell is above level 0, else 0.
+ * eta_out (host, may be NULL) and flags (host) have one entry per cell in mesh
+ * order.  Synchronises. */
+ader_status ader_gradient_flags(ader_ctx* ctx, int var, double refine_above, double coarsen_below,
+                                double* eta_out, int8_t* flags);
+
 /* Skeleton batch: transition cells plus cells with flags[c] > 0 (flags may be
  * NULL).  Host call; uploads the new lists (synchronous). */
 ader_status ader_classify(ader_ctx* ctx, const int8_t* flags);

@@ -38,7 +38,7 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_batch_set_state", "ader_batch_get_state", "ader_batch_compute_dt",
            "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
            "ader_batch_status_word", "ader_batch_launch_count", "ader_adjoint_step",
-           "ader_sample", "ader_sample_adjoint"]
+           "ader_sample", "ader_sample_adjoint", "ader_gradient_flags"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -120,6 +120,8 @@ def lib():
         "ader_batch_status_word": ([_vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "ader_batch_launch_count": ([_vp, _i64p], ctypes.c_int),
         "ader_adjoint_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "ader_gradient_flags": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp],
+                                ctypes.c_int),
         "ader_sample": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
         "ader_sample_adjoint": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
                                 ctypes.c_int),
@@ -416,3 +418,12 @@ def ader_sample_adjoint(ctx, npts, cells_dev, weights_dev, var, values_dev, fiel
     _check(ctx, lib().ader_sample_adjoint(ctx, npts, _ptr(cells_dev), _ptr(weights_dev), var,
                                           _ptr(values_dev), _ptr(field_dev), stream),
            "ader_sample_adjoint")
+
+
+def ader_gradient_flags(ctx, var, refine_above, coarsen_below):
+    ncells = ader_mesh_info(ctx)[0]
+    eta = np.zeros(ncells, dtype=np.float64)
+    flags = np.zeros(ncells, dtype=np.int8)
+    _check(ctx, lib().ader_gradient_flags(ctx, var, float(refine_above), float(coarsen_below),
+                                          _ptr(eta), _ptr(flags)), "ader_gradient_flags")
+    return eta, flags

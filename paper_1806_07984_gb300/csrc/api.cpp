@@ -571,6 +571,46 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   return ADER_OK;
 }
 
+ader_status ader_gradient_flags(ader_ctx* c, int var, double refine_above, double coarsen_below,
+                                double* eta_out, int8_t* flags) {
+  if (!c || !flags || var < 0 || var >= c->M || !(refine_above >= coarsen_below)) return ADER_ERR_ARG;
+  const int64_t C = int64_t(c->tree.cells.size());
+  double* d_eta = nullptr;
+  CK(cudaMalloc(&d_eta, sizeof(double) * size_t(std::max<int64_t>(C, 1))), "cudaMalloc eta");
+  IndicatorArgs a{};
+  a.u = c->u;
+  a.level = c->level;
+  a.ncells = C;
+  a.var = var;
+  a.eta = d_eta;
+  std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
+  a.B = c->B;
+  const int N = c->cfg.order;
+  cudaError_t e;
+  if (c->cfg.pde == ADER_EULER)
+    e = c->cfg.dim == 2 ? indicator_euler2d(N, a, nullptr) : indicator_euler3d(N, a, nullptr);
+  else
+    e = c->cfg.dim == 2 ? indicator_acoustics2d(N, a, nullptr) : indicator_acoustics3d(N, a, nullptr);
+  c->launches += C > 0 ? 1 : 0;
+  std::vector<double> eta(static_cast<size_t>(C));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && C > 0)
+    e = cudaMemcpy(eta.data(), d_eta, sizeof(double) * size_t(C), cudaMemcpyDeviceToHost);
+  cudaFree(d_eta);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient indicator");
+  for (int64_t i = 0; i < C; ++i) {
+    const int lv = c->tree.cells[size_t(i)].level;
+    int8_t f = 0;
+    if (eta[size_t(i)] > refine_above && lv < c->cfg.max_level)
+      f = 1;
+    else if (eta[size_t(i)] < coarsen_below && lv > 0)
+      f = -1;
+    flags[i] = f;
+    if (eta_out) eta_out[i] = eta[size_t(i)];
+  }
+  return ADER_OK;
+}
+
 ader_status ader_sphere_flags(ader_ctx* c, const double center[3], double radius, int8_t* flags) {
   if (!c || !center || !flags) return ADER_ERR_ARG;
   c->tree.sphere_flags(center, radius, c->cfg.lo, c->cfg.hi, flags);

@@ -8,7 +8,8 @@ namespace ader {
   cudaError_t predict_##TAG(int order, Precision prec, const PredictArgs& a, cudaStream_t s); \
   cudaError_t faces_##TAG(int order, int which, const RiemannArgs& a, cudaStream_t s);        \
   cudaError_t correct_##TAG(int order, bool update, const CorrectArgs& a, cudaStream_t s);    \
-  cudaError_t transfer_##TAG(int order, const TransferArgs& a, cudaStream_t s);
+  cudaError_t transfer_##TAG(int order, const TransferArgs& a, cudaStream_t s);              \
+  cudaError_t indicator_##TAG(int order, const IndicatorArgs& a, cudaStream_t s);
 
 ADER_DECLARE(euler2d)
 ADER_DECLARE(euler3d)

@@ -363,6 +363,52 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::NS) transfer_kernel(cons
   for (int v = 0; v < M; ++v) a.u_new[(c * M + v) * NS + node] = acc[v];
 }
 
+// Refinement indicator (epilogue of the corrector): per cell the largest
+// h |grad q| over its nodes, for one variable q.
+template <int DIM, int N, int M>
+__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kernel(const IndicatorArgs a) {
+  using SH = PredictShape<DIM, N>;
+  constexpr int n = SH::n, NS = SH::NS, CPB = SH::CPB;
+  __shared__ double q[CPB][NS];
+  __shared__ double sD[n * n];
+  __shared__ unsigned long long emax[CPB];
+  const int tid = threadIdx.x;
+  const int cl = tid / NS;
+  const int node = tid - cl * NS;
+  const int64_t cell = int64_t(blockIdx.x) * CPB + cl;
+  const bool valid = cell < a.ncells;
+  for (int t = tid; t < n * n; t += blockDim.x) sD[t] = a.B.D[t / n][t % n];
+  q[cl][node] = valid ? a.u[(cell * M + a.var) * NS + node] : 0.0;
+  if (node == 0) emax[cl] = 0ull;
+  __syncthreads();
+  const int id[3] = {node % n, (node / n) % n, node / (n * n)};
+  const int stride[3] = {1, n, n * n};
+  const int lv = valid ? int(a.level[cell]) : 0;
+  double g2 = 0.0, hmax = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int base = node - id[d] * stride[d];
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < n; ++j) s = fma(sD[id[d] * n + j], q[cl][base + j * stride[d]], s);
+    s *= a.inv_h[lv][d];
+    g2 = fma(s, s, g2);
+    hmax = fmax(hmax, 1.0 / a.inv_h[lv][d]);
+  }
+  const double eta = sqrt(g2) * hmax;
+  if (valid) atomicMax(&emax[cl], static_cast<unsigned long long>(__double_as_longlong(eta)));
+  __syncthreads();
+  if (valid && node == 0) a.eta[cell] = __longlong_as_double(static_cast<long long>(emax[cl]));
+}
+
+template <int DIM, int N, int M>
+cudaError_t launch_indicator_t(const IndicatorArgs& a, cudaStream_t s) {
+  using SH = PredictShape<DIM, N>;
+  if (a.ncells == 0) return cudaSuccess;
+  indicator_kernel<DIM, N, M><<<unsigned((a.ncells + SH::CPB - 1) / SH::CPB), SH::THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int DIM, int N, class PDE>
 cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
   constexpr int S = DIM == 3 ? 9 : 3;

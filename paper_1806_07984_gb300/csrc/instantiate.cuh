@@ -46,6 +46,10 @@ cudaError_t with_order(int order, F&& f) {
     return with_order(order,                                                                   \
                       [&](auto N) { return launch_transfer_t<DIM, N.value, PDE::M>(a, s); });  \
   }                                                                                            \
+  cudaError_t indicator_##TAG(int order, const IndicatorArgs& a, cudaStream_t s) {             \
+    return with_order(order,                                                                   \
+                      [&](auto N) { return launch_indicator_t<DIM, N.value, PDE::M>(a, s); }); \
+  }                                                                                            \
   }
 
 // Cauchy-Kowalevski predictor (linear PDEs only).

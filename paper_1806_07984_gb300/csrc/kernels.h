@@ -70,6 +70,18 @@ struct CorrectArgs {
   BasisTables B;
 };
 
+// Solution-based refinement indicator: eta[c] = max over the nodes of h_c
+// |grad u_var| with h_c = max_d h_d (first derivatives by D along each axis).
+struct IndicatorArgs {
+  const double* u;
+  const int8_t* level;
+  int64_t ncells;
+  int var;
+  double* eta;
+  double inv_h[kMaxLevels][3];
+  BasisTables B;
+};
+
 struct TransferArgs {
   const double* u_old;
   double* u_new;

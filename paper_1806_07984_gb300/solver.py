@@ -134,6 +134,9 @@ class Solver:
     def classify(self, flags=None):
         A.ader_classify(self.ctx, flags)
 
+    def gradient_flags(self, var, refine_above, coarsen_below):
+        return A.ader_gradient_flags(self.ctx, var, refine_above, coarsen_below)
+
     def sphere_flags(self, center, radius):
         return A.ader_sphere_flags(self.ctx, center, radius)
 

@@ -179,3 +179,42 @@ def test_cauchy_kowalevski_predictor(dim, order, precision, tol):
     base, lvl = (9, 2) if dim == 2 else ((3, 2) if order < 7 else (2, 0))
     stage_parity(dim, order, "acoustics", base, lvl, [c] * lvl, 0.12, seed=70 + order, tol=tol,
                  precision=precision, predictor="ck")
+
+
+def test_solution_based_remesh_parity():
+    """Solution-based AMR (first-derivative criterion on the density): the
+    device indicator equals the oracle's, flags agree away from the
+    thresholds, and a run that remeshes by the criterion every 2 steps keeps
+    the same mesh and state as the oracle."""
+    from oracle import criterion
+    dim, order = 3, 3
+    solver, om, perm = build_pair(dim, order, "euler", 5, 2)
+    B = obasis.Basis(order)
+    P = opde.Euler(dim)
+    u = state_from(om, B, lambda X: workloads.density_bubble(X, sigma=0.08))
+    solver.set_state(u[perm])
+    refine_above, coarsen_below = 0.04, 0.01
+    changed = 0
+    for rnd in range(3):
+        eta_o, fl_o = criterion.gradient_flags(om, u, B, 0, refine_above, coarsen_below)
+        eta_g, fl_g = solver.gradient_flags(0, refine_above, coarsen_below)
+        assert rel_l2(eta_g, eta_o[perm]) < 1e-12
+        near = (np.abs(eta_o[perm] - refine_above) < 1e-10) | (np.abs(eta_o[perm] - coarsen_below) < 1e-10)
+        assert np.array_equal(fl_g[~near], fl_o[perm][~near])
+        before = len(om.cells)
+        solver.remesh(fl_o[perm])
+        u = om.remesh(u, fl_o, B)
+        changed += len(om.cells) != before
+        keys = lib_keys(solver)
+        assert sorted(keys) == om.cells
+        perm = np.array([om.index[k] for k in keys])
+        h = om.cell_widths()
+        dt = oader.cfl_dt(u, h, P, order, cfl=workloads.ADER_CFL[order])
+        solver.set_dt(dt)
+        for _ in range(2):
+            out = ostep.step(om, u, dt, P, B)
+            u, dt = out.u, out.dt_next
+        solver.step(2)
+        assert rel_l2(solver.get_state().cpu().numpy(), u[perm]) < TOL64
+    assert changed >= 2
+    assert solver.status() == 0

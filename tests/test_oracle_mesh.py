@@ -166,3 +166,23 @@ def test_prolong_face_equals_extrapolated_prolong_volume(dim):
                 vol = ader.prolong_volume(x, tuple(full), B)
                 ref = ader.face_values(vol, dr, side, B)
                 assert np.allclose(ader.prolong_face(face, s, B, dim), ref, atol=1e-13)
+
+
+def test_gradient_indicator_of_linear_and_quadratic_fields():
+    """eta = h |grad q| is exact for a linear field and for x^2 at the node of
+    largest x (polynomials of degree <= N are differentiated exactly)."""
+    from oracle import criterion
+    N = 3
+    B = basis.Basis(N)
+    m = meshmod.Mesh(2, (3, 3), 1)
+    X = m.node_coords(B.xi)
+    u = np.stack([3.0 * X[0] - 4.0 * X[1], X[0] ** 2], axis=1)
+    h = m.cell_widths()
+    eta = criterion.gradient_indicator(u, h, B, 0)
+    assert np.allclose(eta, 5.0 * h[:, 0], rtol=1e-12)
+    eta2 = criterion.gradient_indicator(u, h, B, 1)
+    xmax = (X[0].reshape(len(m.cells), -1)).max(axis=1)
+    assert np.allclose(eta2, 2.0 * xmax * h[:, 0], rtol=1e-12)
+    _, fl = criterion.gradient_flags(m, u, B, 0, 5.0 / 4, 5.0 / 10)
+    assert fl.tolist() == [1 if 5.0 * hh > 5.0 / 4 else (-1 if k[0] > 0 and 5.0 * hh < 0.5 else 0)
+                           for hh, k in zip(h[:, 0], m.cells)]
