@@ -420,9 +420,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="euler3d-n5-amr", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64",
-                    choices=["fp64", "fp32", "tf32", "tf32x3", "bf16x3"])
+                    choices=["fp64", "fp32", "tf32", "tf32x3", "bf16x3", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mixed", default="fp32,tf32x3,bf16x3,tf32",
+    ap.add_argument("--mixed", default="df64,fp32,tf32x3,bf16x3,tf32",
                     help="predictor precisions compared with FP64 ('' to skip)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -546,8 +546,9 @@ def main():
             sm_.close()
         mixed["fp64_l2_rel_err_vs_exact"] = err64
         mixed["vars"] = names[:len(err64)]
-        mixed["note"] = ("FP32 predictor arithmetic (CUDA cores or tensor cores), FP64 state, "
-                         "faces, Riemann, corrector and CFL reduction")
+        mixed["note"] = ("predictor arithmetic: df64 = double-float on the FP32 pipes, fp32 = FP32 "
+                         "CUDA cores, tf32/tf32x3/bf16x3 = tcgen05 tensor cores; FP64 state, faces, "
+                         "Riemann, corrector and CFL reduction in every mode")
         del state64
     else:
         s.close()

@@ -72,13 +72,17 @@ typedef enum { ADER_EULER = 0, ADER_ACOUSTICS = 1 } ader_pde;
  *   ADER_TF32X3  tensor cores with hi/lo TF32 splits (three products),
  *                close to FP32 accuracy
  *   ADER_BF16X3  tensor cores with hi/lo BF16 splits (three products)
+ *   ADER_DF64    double-float: every predictor value is a pair of FP32 numbers
+ *                (about 48 significant bits) computed with error-free
+ *                transformations on the FP32 pipes
  * The tensor-core modes are available for 3D Euler at orders 5..7. */
 typedef enum {
   ADER_FP64 = 0,
   ADER_FP32 = 1,
   ADER_TF32 = 2,
   ADER_TF32X3 = 3,
-  ADER_BF16X3 = 4
+  ADER_BF16X3 = 4,
+  ADER_DF64 = 5
 } ader_precision;
 
 typedef enum { ADER_ALL = 0, ADER_SKELETON = 1, ADER_ENCLAVE = 2 } ader_set;

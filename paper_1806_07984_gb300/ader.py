@@ -19,9 +19,9 @@ STATUS_NAMES = {0: "ADER_OK", -1: "ADER_ERR_ARG", -2: "ADER_ERR_CUDA", -3: "ADER
                 -4: "ADER_ERR_NONPHYSICAL", -5: "ADER_ERR_PICARD", -6: "ADER_ERR_TIMEOUT",
                 -7: "ADER_ERR_MESH"}
 ADER_EULER, ADER_ACOUSTICS = 0, 1
-ADER_FP64, ADER_FP32, ADER_TF32, ADER_TF32X3, ADER_BF16X3 = 0, 1, 2, 3, 4
+ADER_FP64, ADER_FP32, ADER_TF32, ADER_TF32X3, ADER_BF16X3, ADER_DF64 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": ADER_FP64, "fp32": ADER_FP32, "tf32": ADER_TF32, "tf32x3": ADER_TF32X3,
-              "bf16x3": ADER_BF16X3}
+              "bf16x3": ADER_BF16X3, "df64": ADER_DF64}
 ADER_ALL, ADER_SKELETON, ADER_ENCLAVE = 0, 1, 2
 ADER_PREDICTOR_PICARD, ADER_PREDICTOR_CK = 0, 1
 ADER_FIELD_U, ADER_FIELD_USTAR, ADER_FIELD_FACE_Q, ADER_FIELD_FACE_F, ADER_FIELD_FSTAR = range(5)

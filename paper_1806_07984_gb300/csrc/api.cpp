@@ -281,8 +281,9 @@ bool valid_config(const ader_config* cfg, std::string* why) {
   const int m = cfg->pde == ADER_EULER ? cfg->dim + 2 : cfg->dim + 1;
   if (cfg->nvar != m) return *why = "nvar does not match the pde", false;
   if (cfg->max_level < 0 || cfg->max_level > kMaxLevels - 2) return *why = "max_level out of range", false;
-  if (cfg->prec < ADER_FP64 || cfg->prec > ADER_BF16X3) return *why = "unknown precision", false;
-  if (cfg->prec >= ADER_TF32 && !(cfg->dim == 3 && cfg->pde == ADER_EULER && cfg->order >= 5))
+  if (cfg->prec < ADER_FP64 || cfg->prec > ADER_DF64) return *why = "unknown precision", false;
+  if (cfg->prec >= ADER_TF32 && cfg->prec <= ADER_BF16X3 &&
+      !(cfg->dim == 3 && cfg->pde == ADER_EULER && cfg->order >= 5))
     return *why = "tensor-core predictor: 3D Euler, order 5..7", false;
   if (!(cfg->cfl > 0.0)) return *why = "cfl must be positive", false;
   for (int d = 0; d < cfg->dim; ++d) {

@@ -28,8 +28,9 @@ cudaError_t with_order(int order, F&& f) {
   namespace ader {                                                                             \
   cudaError_t predict_##TAG(int order, Precision prec, const PredictArgs& a, cudaStream_t s) { \
     return with_order(order, [&](auto N) {                                                     \
-      return prec == Precision::kFP64 ? launch_predict_t<DIM, N.value, PDE, double>(a, s)      \
-                                      : launch_predict_t<DIM, N.value, PDE, float>(a, s);      \
+      return prec == Precision::kFP64   ? launch_predict_t<DIM, N.value, PDE, double>(a, s)    \
+             : prec == Precision::kDF64 ? launch_predict_t<DIM, N.value, PDE, df64>(a, s)      \
+                                        : launch_predict_t<DIM, N.value, PDE, float>(a, s);    \
     });                                                                                        \
   }                                                                                            \
   cudaError_t faces_##TAG(int order, int which, const RiemannArgs& a, cudaStream_t s) {        \

@@ -93,7 +93,7 @@ struct TransferArgs {
   BasisTables B;
 };
 
-enum class Precision { kFP64 = 0, kFP32 = 1, kTF32 = 2, kTF32x3 = 3, kBF16x3 = 4 };
+enum class Precision { kFP64 = 0, kFP32 = 1, kTF32 = 2, kTF32x3 = 3, kBF16x3 = 4, kDF64 = 5 };
 
 // Returns cudaErrorInvalidValue when (dim, order, pde, precision) has no
 // compiled kernel.

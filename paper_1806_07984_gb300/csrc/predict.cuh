@@ -21,6 +21,7 @@
 #pragma once
 #include <type_traits>
 
+#include "df64.cuh"
 #include "kernels.h"
 #include "pde.cuh"
 #include "tc.cuh"
@@ -142,7 +143,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   // FP32: this thread's rows of D/h_d live in registers for every slice
   // (shared-memory bandwidth bounds that variant).  FP64: they stay in shared
   // memory (the FP64 pipe bounds that variant and registers are scarce).
-  constexpr bool kDinRegs = !std::is_same<Real, double>::value;
+  constexpr bool kDinRegs = std::is_same<Real, float>::value;
   constexpr int kDr = kDinRegs ? n : 1;
   __syncthreads();
   Real Dr[DIM][kDr];

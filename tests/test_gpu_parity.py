@@ -218,3 +218,15 @@ def test_solution_based_remesh_parity():
         assert rel_l2(solver.get_state().cpu().numpy(), u[perm]) < TOL64
     assert changed >= 2
     assert solver.status() == 0
+
+
+# Double-float predictor (pairs of FP32 values, ~48 significant bits): stated
+# bound 1e-11 on every field of one step against the FP64 oracle.
+TOL_DF64 = 1e-11
+
+
+@pytest.mark.parametrize("dim,order,base,lvl", [(3, 5, 3, 1), (2, 3, 9, 2), (3, 3, 3, 2)])
+def test_double_float_predictor_bound(dim, order, base, lvl):
+    c = (0.5, 0.5, 0.5)[:dim]
+    stage_parity(dim, order, "euler", base, lvl, [c] * lvl, 0.2, seed=80 + order, tol=TOL_DF64,
+                 precision="df64")
