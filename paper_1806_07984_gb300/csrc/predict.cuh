@@ -495,8 +495,16 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   }
 }
 
+// Resident CTAs per SM the register allocation must allow: the double-float
+// variant's long dependent chains need two CTAs to keep the FP32 pipes busy.
+template <class Real, int NS>
+struct PredictMinBlocks {
+  static constexpr int value = (std::is_same<Real, df64>::value && NS <= 216) ? 2 : 1;
+};
+
 template <int DIM, int N, class PDE, class Real, int SCHEME = 0>
-__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
+__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS,
+                                  PredictMinBlocks<Real, PredictShape<DIM, N>::NS>::value)
     predict_kernel(const PredictArgs a) {
   using S = PredictShape<DIM, N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
