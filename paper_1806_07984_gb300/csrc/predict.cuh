@@ -144,6 +144,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   // (shared-memory bandwidth bounds that variant).  FP64: they stay in shared
   // memory (the FP64 pipe bounds that variant and registers are scarce).
   constexpr bool kDinRegs = std::is_same<Real, float>::value;
+  constexpr bool kRollSlices = std::is_same<Real, df64>::value;
   constexpr int kDr = kDinRegs ? n : 1;
   __syncthreads();
   Real Dr[DIM][kDr];
@@ -358,8 +359,8 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       for (int k = 0; k < n; ++k)
 #pragma unroll
         for (int v = 0; v < M; ++v) acc[k][v] = uu[v];
-#pragma unroll
-      for (int l = 0; l < n; ++l) {
+      // one time slice of the Picard update: acc_k += -dt Mt[k][l] g(q_l)
+      auto slice = [&](int l) {
         Real g[M];
         divergence(q[l], g);
 #pragma unroll
@@ -368,6 +369,15 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
           for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
         }
+      };
+      if constexpr (kRollSlices) {
+        // double-float code is long: keep one copy of the slice body so the
+        // kernel fits the instruction cache (q_l is then read from L1)
+#pragma unroll 1
+        for (int l = 0; l < n; ++l) slice(l);
+      } else {
+#pragma unroll
+        for (int l = 0; l < n; ++l) slice(l);
       }
 #pragma unroll
       for (int k = 0; k < n; ++k)
@@ -381,8 +391,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
       for (int v = 0; v < M; ++v) Fb[d][v] = Real(0);
-#pragma unroll
-    for (int k = 0; k < n; ++k) {
+    auto average = [&](int k) {
       Real f[DIM][M];
       PDE::fluxes(q[k], f, gamma);
       const Real wk = sw[k];
@@ -392,6 +401,13 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       for (int d = 0; d < DIM; ++d)
 #pragma unroll
         for (int v = 0; v < M; ++v) Fb[d][v] = fma(wk, f[d][v], Fb[d][v]);
+    };
+    if constexpr (kRollSlices) {
+#pragma unroll 1
+      for (int k = 0; k < n; ++k) average(k);
+    } else {
+#pragma unroll
+      for (int k = 0; k < n; ++k) average(k);
     }
   }
   bool finite = true;

@@ -225,8 +225,11 @@ def test_solution_based_remesh_parity():
 TOL_DF64 = 1e-11
 
 
-@pytest.mark.parametrize("dim,order,base,lvl", [(3, 5, 3, 1), (2, 3, 9, 2), (3, 3, 3, 2)])
-def test_double_float_predictor_bound(dim, order, base, lvl):
+@pytest.mark.parametrize("dim,order,pde,base,lvl", [
+    (3, 5, "euler", 3, 1), (2, 3, "euler", 9, 2), (3, 3, "euler", 3, 2), (3, 4, "euler", 3, 1),
+    (3, 6, "euler", 3, 1), (3, 7, "euler", 3, 1), (2, 7, "euler", 6, 1),
+    (3, 5, "acoustics", 3, 1), (2, 4, "acoustics", 9, 1)])
+def test_double_float_predictor_bound(dim, order, pde, base, lvl):
     c = (0.5, 0.5, 0.5)[:dim]
-    stage_parity(dim, order, "euler", base, lvl, [c] * lvl, 0.2, seed=80 + order, tol=TOL_DF64,
+    stage_parity(dim, order, pde, base, lvl, [c] * lvl, 0.2, seed=80 + order, tol=TOL_DF64,
                  precision="df64")
