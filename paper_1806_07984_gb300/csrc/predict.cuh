@@ -297,20 +297,37 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < M; ++v) g[v] = Real(0);
+    if constexpr (kRollSlices) {
+      // one copy of the line contraction, the direction chosen at run time
+#pragma unroll 1
+      for (int d = 0; d < DIM; ++d) {
+        const int sd = d == 0 ? 1 : (d == 1 ? n : n * n);
+        const int idd = d == 0 ? id[0] : (d == 1 ? id[1] : id[2]);
+        const Real* line0 = my_fb + d * M * NS + node - idd * sd;
+        const Real* drow = &sDh[cl][d][idd * n];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const int base = node - id[d] * stride[d];
+        for (int v = 0; v < M; ++v) {
+          const Real* line = line0 + v * NS;
 #pragma unroll
-      for (int v = 0; v < M; ++v) {
-        const Real* line = my_fb + (d * M + v) * NS + base;
+          for (int j = 0; j < n; ++j) g[v] = fma(drow[j], line[j * sd], g[v]);
+        }
+      }
+    } else {
 #pragma unroll
-        for (int j = 0; j < n; ++j) {
-          Real dj;
-          if constexpr (kDinRegs)
-            dj = Dr[d][j < kDr ? j : 0];
-          else
-            dj = sDh[cl][d][id[d] * n + j];
-          g[v] = fma(dj, line[j * stride[d]], g[v]);
+      for (int d = 0; d < DIM; ++d) {
+        const int base = node - id[d] * stride[d];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const Real* line = my_fb + (d * M + v) * NS + base;
+#pragma unroll
+          for (int j = 0; j < n; ++j) {
+            Real dj;
+            if constexpr (kDinRegs)
+              dj = Dr[d][j < kDr ? j : 0];
+            else
+              dj = sDh[cl][d][id[d] * n + j];
+            g[v] = fma(dj, line[j * stride[d]], g[v]);
+          }
         }
       }
     }
