@@ -16,6 +16,11 @@ Table 1) on synthetic smooth data:
   0.05 with seeded amplitudes in [0.5, 1] and centres in [0, 1]^3, v = 0.
 * ``random_euler``      - seeded perturbations of a uniform Euler state with
   positive density and pressure (parity inputs).
+* ``circular_explosion`` - 2D/3D Euler with shocks for the subcell limiter
+  (the paper's Euler-with-shocks runs use a circular explosion; its data are
+  not given): rho = 1, p = 1 inside a ball of radius 0.25 around the centre,
+  rho = 0.125, p = 0.1 outside, at rest (the classic Sod states), the jump
+  optionally smoothed by a tanh profile.
 
 All states are conserved variables in the layout [var, ...] of the coordinate
 arrays (Euler: rho, rho v_1..rho v_d, E; acoustics: p, v_1..v_d).
@@ -72,6 +77,28 @@ def density_bubble(coords, t=0.0, amp=0.2, sigma=0.05, center=(0.5, 0.5, 0.5),
     rho = 1.0 + amp * np.exp(-r2 / sigma ** 2)
     vel_arr = [np.full_like(rho, vel[a]) for a in range(dim)]
     return _conserved(rho, vel_arr, np.ones_like(rho), gamma)
+
+
+EXPLOSION_RADIUS = 0.25
+
+
+def circular_explosion(coords, center=(0.5, 0.5, 0.5), radius=EXPLOSION_RADIUS, width=0.0,
+                       gamma=GAMMA):
+    """Conserved Euler state of the circular (spherical in 3D) explosion; with
+    width > 0 the jump is smoothed to 0.5 (1 + tanh((radius - r) / width))."""
+    dim = len(coords)
+    r2 = 0.0
+    for a in range(dim):
+        d = _periodic_delta(coords[a], center[a])
+        r2 = r2 + d * d
+    if width > 0.0:
+        inside = 0.5 * (1.0 + np.tanh((radius - np.sqrt(r2)) / width))
+    else:
+        inside = (r2 < radius * radius).astype(np.float64)
+    rho = 0.125 + 0.875 * inside
+    p = 0.1 + 0.9 * inside
+    vel = [np.zeros_like(rho) for _ in range(dim)]
+    return _conserved(rho, vel, p, gamma)
 
 
 def sphere_center(t, center=(0.5, 0.5, 0.5), vel=(1.0, 1.0, 1.0)):
