@@ -115,6 +115,10 @@ typedef struct {
   int picard_iters;  /* Picard iterations; 0 selects order + 1 */
   ader_precision prec;
   ader_predictor predictor;  /* ADER_PREDICTOR_CK: acoustics, FP64 or FP32 */
+  int limiter;               /* 1: a posteriori subcell FV limiter in every corrector
+                                (2D orders 1..7, 3D orders 1..5); see ader_limiter_flags */
+  double limiter_delta0;     /* relaxed maximum principle: delta = max(delta0, eps (max - min)); */
+  double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
 } ader_config;
 
 typedef struct ader_ctx ader_ctx;
@@ -174,7 +178,25 @@ ader_status ader_riemann(ader_ctx* ctx, ader_set set, void* stream);
 
 /* C_Corr (Algorithm 1 third loop) on all cells: u = u* + face lifting of F*,
  * then *dt_next_dev = cfl / max sum_d lambda_d(u) / h_d (CTA maxima by warp
- * shuffles, one atomicMax each).  dt_next_dev may equal dt_dev. */
+ * shuffles, one atomicMax each).  dt_next_dev may equal dt_dev.
+ *
+ * With cfg.limiter set, the corrected state is a candidate and the a
+ * posteriori subcell finite-volume limiter follows (Sec. 4, "Finite Volumes":
+ * FV on (2N+1)^d subcell patches as the limiter of ADER-DG; detection after
+ * Dumbser et al., J. Comput. Phys. 278 (2014)):
+ *   - a cell is troubled when its candidate has a non-finite value, (Euler)
+ *     rho <= 0 or p <= 0 at a node or subcell average, or a subcell average
+ *     outside [min_V - delta, max_V + delta], V = the subcell averages of u(T)
+ *     in the cell and its conforming face neighbours;
+ *   - a troubled cell redoes its step from u(T) by one first-order Rusanov FV
+ *     step on its subcells (halo: the neighbours' adjacent subcell layers) and
+ *     gets its nodal values back by least squares; an unlimited neighbour
+ *     lifts the L2 projection of the FV subface fluxes instead of its F*;
+ *   - a troubled cell with a non-conforming face keeps its candidate and sets
+ *     status bit 5;
+ *   - dt_next comes from the final nodes and the limited cells' subcells.
+ * Candidate-stage status bits (predictor, Riemann, corrector) go to an
+ * internal word in this mode; the status word reports the final state. */
 ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_dev, void* stream);
 
 /* nsteps full steps.  Each step runs the skeleton predictor, transition
@@ -214,8 +236,24 @@ ader_status ader_sphere_flags(ader_ctx* ctx, const double center[3], double radi
 /* Synchronise the context's streams and return the device status word
  * (bit 0 non-finite predictor, bit 1 non-physical state, bit 2 non-finite
  * CFL rate, bit 3 bad transfer index, bit 4 a bounded wait for the tensor
- * cores expired); clears it. */
+ * cores expired, bit 5 a troubled cell at a resolution transition kept its
+ * DG candidate); clears it. */
 ader_status ader_status_word(ader_ctx* ctx, uint32_t* out);
+
+/* Limiter outcome of the last corrector, one uint32 per cell in mesh order
+ * (flags: device array when on_device, else host; the host copy
+ * synchronises): bit 0 the cell's step was redone by FV on its subcell
+ * patch, bit 1 an unlimited cell lifted FV subface fluxes on a face, bit 2
+ * troubled at a resolution transition (DG candidate kept).  *nlimited (host,
+ * may be NULL) receives the number of cells with bit 0 (synchronises).
+ * ADER_ERR_ARG when the context has no limiter. */
+ader_status ader_limiter_flags(ader_ctx* ctx, uint32_t* flags, int on_device, int64_t* nlimited,
+                               void* stream);
+
+/* Treat the cells with force[c] != 0 (host array, one byte per cell in mesh
+ * order) as troubled in every following corrector; NULL clears.  A remesh
+ * clears it too.  ADER_ERR_ARG when the context has no limiter. */
+ader_status ader_limiter_force(ader_ctx* ctx, const uint8_t* force);
 
 /* Discrete adjoint of one step: *lambda_out = A^T lambda_in, where A is the
  * linear map u(T) -> u(T+dt) of ader_step/ader_predict+ader_riemann+

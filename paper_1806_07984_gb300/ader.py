@@ -38,7 +38,8 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_batch_set_state", "ader_batch_get_state", "ader_batch_compute_dt",
            "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
            "ader_batch_status_word", "ader_batch_launch_count", "ader_adjoint_step",
-           "ader_sample", "ader_sample_adjoint", "ader_gradient_flags"]
+           "ader_sample", "ader_sample_adjoint", "ader_gradient_flags", "ader_limiter_flags",
+           "ader_limiter_force"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -58,7 +59,9 @@ class ader_config(ctypes.Structure):
                 ("pde", ctypes.c_int), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("base", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("max_level", ctypes.c_int),
-                ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int), ("predictor", ctypes.c_int)]
+                ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int), ("predictor", ctypes.c_int),
+                ("limiter", ctypes.c_int), ("limiter_delta0", ctypes.c_double),
+                ("limiter_eps", ctypes.c_double)]
 
 
 _lib = None
@@ -97,6 +100,8 @@ def lib():
         "ader_sphere_flags": ([_vp, _vp, ctypes.c_double, _vp], ctypes.c_int),
         "ader_status_word": ([_vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "ader_launch_count": ([_vp, _i64p], ctypes.c_int),
+        "ader_limiter_flags": ([_vp, _vp, ctypes.c_int, _i64p, _vp], ctypes.c_int),
+        "ader_limiter_force": ([_vp, _vp], ctypes.c_int),
         "ader_mesh_create": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
         "ader_mesh_destroy": ([_vp], None),
         "ader_mesh_adapt": ([_vp, _vp], ctypes.c_int),
@@ -252,6 +257,26 @@ def ader_status_word(ctx):
     v = ctypes.c_uint32()
     _check(ctx, lib().ader_status_word(ctx, ctypes.byref(v)), "ader_status_word")
     return v.value
+
+
+def ader_limiter_flags(ctx, stream=None):
+    """Per-cell limiter flags of the last corrector (host uint32 array) and the
+    number of limited cells."""
+    ncells = ader_mesh_info(ctx)[0]
+    out = np.zeros(ncells, dtype=np.uint32)
+    cnt = ctypes.c_int64()
+    _check(ctx, lib().ader_limiter_flags(ctx, _ptr(out), 0, ctypes.byref(cnt), stream),
+           "ader_limiter_flags")
+    return out, cnt.value
+
+
+def ader_limiter_force(ctx, force):
+    """Cells treated as troubled from now on (bool/uint8 per cell); None clears."""
+    if force is None:
+        _check(ctx, lib().ader_limiter_force(ctx, None), "ader_limiter_force")
+        return
+    f = np.ascontiguousarray(np.asarray(force).astype(np.uint8))
+    _check(ctx, lib().ader_limiter_force(ctx, _ptr(f)), "ader_limiter_force")
 
 
 def ader_launch_count(ctx):

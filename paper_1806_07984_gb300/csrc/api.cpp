@@ -36,6 +36,19 @@ struct ader_ctx {
   unsigned long long* rate = nullptr;
   uint32_t* status = nullptr;
   double* dt_scratch = nullptr;
+  // subcell FV limiter (cfg.limiter): backup of u(T), subcell bounds, flags,
+  // lists, neighbour table, forced cells; the candidate stage reports into
+  // rate_cand / status_cand
+  SubcellTables T{};
+  double *u_old = nullptr, *bounds = nullptr;
+  uint32_t* lim_flags = nullptr;
+  int32_t *lim_list = nullptr, *fix_list = nullptr, *nbr = nullptr;
+  uint8_t* force = nullptr;
+  bool force_set = false;
+  int* lim_counts = nullptr;
+  unsigned long long* rate_cand = nullptr;
+  uint32_t* status_cand = nullptr;
+  int num_sms = 0;
   std::string err;
   int64_t launches = 0;
 };
@@ -142,6 +155,25 @@ ader_status ensure_cells(ader_ctx* c, int64_t need) {
   CK(cudaMalloc(&c->all_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
   CK(cudaMalloc(&c->skel_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
   CK(cudaMalloc(&c->encl_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
+  if (c->cfg.limiter) {
+    for (void* p : {(void*)c->u_old, (void*)c->bounds, (void*)c->lim_flags, (void*)c->lim_list,
+                    (void*)c->fix_list, (void*)c->nbr, (void*)c->force})
+      if (p) cudaFree(p);
+    c->u_old = c->bounds = nullptr;
+    c->lim_flags = nullptr;
+    c->lim_list = c->fix_list = c->nbr = nullptr;
+    c->force = nullptr;
+    CK(cudaMalloc(&c->u_old, cell_bytes * size_t(nc)), "cudaMalloc limiter backup");
+    CK(cudaMalloc(&c->bounds, sizeof(double) * 2 * c->M * size_t(nc)), "cudaMalloc limiter bounds");
+    CK(cudaMalloc(&c->lim_flags, sizeof(uint32_t) * size_t(nc)), "cudaMalloc limiter flags");
+    CK(cudaMalloc(&c->lim_list, sizeof(int32_t) * size_t(nc)), "cudaMalloc limiter lists");
+    CK(cudaMalloc(&c->fix_list, sizeof(int32_t) * size_t(nc)), "cudaMalloc limiter lists");
+    CK(cudaMalloc(&c->nbr, sizeof(int32_t) * 2 * c->cfg.dim * size_t(nc)), "cudaMalloc neighbours");
+    CK(cudaMalloc(&c->force, size_t(nc)), "cudaMalloc limiter force");
+    CK(cudaMemset(c->lim_flags, 0, sizeof(uint32_t) * size_t(nc)), "clear limiter flags");
+    CK(cudaMemset(c->force, 0, size_t(nc)), "clear limiter force");
+    c->force_set = false;
+  }
   c->cap = nc;
   return ADER_OK;
 }
@@ -185,8 +217,23 @@ ader_status upload_mesh(ader_ctx* c) {
     CK(cudaMemcpy(c->child_fine, t.child_fine.data(), sizeof(int32_t) * t.child_fine.size(),
                   cudaMemcpyHostToDevice), "upload children");
   }
+  if (c->cfg.limiter) {
+    // conforming neighbour across each face, -1 across a resolution transition
+    const int F = 2 * c->cfg.dim;
+    std::vector<int32_t> nb(static_cast<size_t>(C) * F, -1);
+    for (const ConfFace& f : t.conf) {
+      nb[size_t(f.left) * F + 2 * f.dir + 1] = f.right;
+      nb[size_t(f.right) * F + 2 * f.dir + 0] = f.left;
+    }
+    CK(cudaMemcpy(c->nbr, nb.data(), sizeof(int32_t) * nb.size(), cudaMemcpyHostToDevice),
+       "upload neighbours");
+  }
   return ADER_OK;
 }
+
+// Status word of the predictor, Riemann and corrector stages: with the
+// limiter these produce a candidate, and its failures are the limiter's input.
+uint32_t* stage_status(ader_ctx* c) { return c->cfg.limiter ? c->status_cand : c->status; }
 
 PredictArgs predict_args(ader_ctx* c, const double* dt, ader_set set) {
   PredictArgs a{};
@@ -208,7 +255,7 @@ PredictArgs predict_args(ader_ctx* c, const double* dt, ader_set set) {
   a.dt = dt;
   a.gamma = c->cfg.gamma;
   a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
-  a.status = c->status;
+  a.status = stage_status(c);
   std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
   a.B = c->B;
   return a;
@@ -223,7 +270,7 @@ RiemannArgs riemann_args(ader_ctx* c) {
   a.child_fine = c->child_fine;
   a.nparents = int64_t(c->tree.parents.size());
   a.gamma = c->cfg.gamma;
-  a.status = c->status;
+  a.status = stage_status(c);
   a.B = c->B;
   return a;
 }
@@ -266,9 +313,65 @@ ader_status enqueue_riemann(ader_ctx* c, ader_set set, cudaStream_t s) {
   return ADER_OK;
 }
 
+LimiterArgs limiter_args(ader_ctx* c, const double* dt) {
+  LimiterArgs a{};
+  a.u = c->u;
+  a.u_old = c->u_old;
+  a.u_backup = c->u_old;
+  a.ustar = c->ustar;
+  a.fstar = c->fstar;
+  a.bounds = c->bounds;
+  a.nbr = c->nbr;
+  a.force = c->force_set ? c->force : nullptr;
+  a.flags = c->lim_flags;
+  a.list = c->lim_list;
+  a.fix_list = c->fix_list;
+  a.counts = c->lim_counts;
+  a.level = c->level;
+  a.ncells = int64_t(c->tree.cells.size());
+  a.dt = dt;
+  a.gamma = c->cfg.gamma;
+  a.delta0 = c->cfg.limiter_delta0 > 0.0 ? c->cfg.limiter_delta0 : 1e-4;
+  a.eps = c->cfg.limiter_eps > 0.0 ? c->cfg.limiter_eps : 1e-3;
+  a.rate_max = c->rate;
+  a.status = c->status;
+  std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
+  a.B = c->B;
+  a.T = c->T;
+  return a;
+}
+
+cudaError_t do_limiter(ader_ctx* c, LimiterKernel which, const LimiterArgs& a, int grid,
+                       cudaStream_t s) {
+  const int pde = c->cfg.pde == ADER_EULER ? 0 : 1;
+  c->launches += 1;
+  return c->cfg.dim == 2 ? launch_limiter_2d(c->cfg.order, pde, which, a, grid, s)
+                         : launch_limiter_3d(c->cfg.order, pde, which, a, grid, s);
+}
+
 ader_status enqueue_correct(ader_ctx* c, const double* dt, double* dt_next, cudaStream_t s) {
   CorrectArgs a = correct_args(c, dt);
-  CK(do_correct(c, true, a, s), "corrector");
+  if (!c->cfg.limiter) {
+    CK(do_correct(c, true, a, s), "corrector");
+    c->launches += 1;
+    CK(launch_finalize_dt(c->rate, c->cfg.cfl, dt_next, c->status, s), "finalize dt");
+    return ADER_OK;
+  }
+  // limiter mode: bounds of u(T) and its backup, the candidate, detection,
+  // FV on the limited cells, the neighbours' corrector with FV face fluxes,
+  // then the CFL rate of the final state
+  const LimiterArgs la = limiter_args(c, dt);
+  const int grid = 2 * c->num_sms;
+  CK(do_limiter(c, LimiterKernel::kBounds, la, grid, s), "limiter bounds");
+  a.rate_max = c->rate_cand;
+  a.status = c->status_cand;
+  CK(do_correct(c, true, a, s), "candidate corrector");
+  CK(cudaMemsetAsync(c->lim_counts, 0, 2 * sizeof(int), s), "clear limiter counts");
+  CK(do_limiter(c, LimiterKernel::kDetect, la, grid, s), "limiter detection");
+  CK(do_limiter(c, LimiterKernel::kFV, la, grid, s), "limiter FV step");
+  CK(do_limiter(c, LimiterKernel::kFix, la, grid, s), "limiter neighbour correction");
+  CorrectArgs r = correct_args(c, dt);
+  CK(do_correct(c, false, r, s), "CFL rate");
   c->launches += 1;
   CK(launch_finalize_dt(c->rate, c->cfg.cfl, dt_next, c->status, s), "finalize dt");
   return ADER_OK;
@@ -298,6 +401,9 @@ bool valid_config(const ader_config* cfg, std::string* why) {
     return *why = "unknown predictor", false;
   if (cfg->predictor == ADER_PREDICTOR_CK && (cfg->pde != ADER_ACOUSTICS || cfg->prec > ADER_FP32))
     return *why = "Cauchy-Kowalevski predictor: linear acoustics, FP64 or FP32", false;
+  if (cfg->limiter != 0 && cfg->limiter != 1) return *why = "limiter must be 0 or 1", false;
+  if (cfg->limiter && cfg->dim == 3 && cfg->order > 5)
+    return *why = "subcell limiter: 3D orders 1..5", false;
   return true;
 }
 
@@ -367,6 +473,21 @@ ader_status ader_init(const ader_config* cfg, ader_ctx** out) {
   if (cudaMemset(c->rate, 0, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(uint32_t)) != cudaSuccess)
     return fail(ADER_ERR_CUDA);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(ADER_ERR_CUDA);
+  if (cfg->limiter) {
+    make_subcells(c->n, &c->T);
+    if (cudaMalloc(&c->lim_counts, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->rate_cand, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->status_cand, sizeof(uint32_t)) != cudaSuccess)
+      return fail(ADER_ERR_OOM);
+    if (cudaMemset(c->lim_counts, 0, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->rate_cand, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->status_cand, 0, sizeof(uint32_t)) != cudaSuccess)
+      return fail(ADER_ERR_CUDA);
+  }
   st = upload_mesh(c);
   if (st != ADER_OK) return fail(st);
   const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
@@ -383,7 +504,10 @@ void ader_destroy(ader_ctx* c) {
   for (void* p : {(void*)c->u, (void*)c->ustar, (void*)c->faceQ, (void*)c->faceF, (void*)c->fstar,
                   (void*)c->level, (void*)c->all_cells, (void*)c->skel_cells, (void*)c->encl_cells,
                   (void*)c->conf, (void*)c->parents, (void*)c->child_fine, (void*)c->rate,
-                  (void*)c->status, (void*)c->dt_scratch})
+                  (void*)c->status, (void*)c->dt_scratch, (void*)c->u_old, (void*)c->bounds,
+                  (void*)c->lim_flags, (void*)c->lim_list, (void*)c->fix_list, (void*)c->nbr,
+                  (void*)c->force, (void*)c->lim_counts, (void*)c->rate_cand,
+                  (void*)c->status_cand})
     if (p) cudaFree(p);
   for (cudaEvent_t e : {c->ev_begin, c->ev_step, c->ev_lo, c->ev_end})
     if (e) cudaEventDestroy(e);
@@ -534,6 +658,7 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
     return ADER_ERR_MESH;
   }
   const int64_t C_new = int64_t(c->tree.cells.size());
+  c->force_set = false;
   // keep the old state while the cell-sized buffers grow
   const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
   double* old_u = nullptr;
@@ -675,6 +800,37 @@ ader_status ader_sample_adjoint(ader_ctx* c, int npts, const int32_t* cells, con
   c->launches += npts > 0 ? 1 : 0;
   CK(launch_sample_adjoint(field, c->M, c->NS, var, npts, cells, weights, values,
                            static_cast<cudaStream_t>(stream)), "sample adjoint");
+  return ADER_OK;
+}
+
+ader_status ader_limiter_flags(ader_ctx* c, uint32_t* flags, int on_device, int64_t* nlimited,
+                               void* stream) {
+  if (!c || !c->cfg.limiter) return ADER_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t C = c->tree.cells.size();
+  if (flags)
+    CK(cudaMemcpyAsync(flags, c->lim_flags, sizeof(uint32_t) * C,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+       "copy limiter flags");
+  if (nlimited) {
+    int cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(cnt, c->lim_counts, sizeof(cnt), cudaMemcpyDeviceToHost, s), "limiter count");
+    CK(cudaStreamSynchronize(s), "limiter count sync");
+    *nlimited = cnt[0];
+  }
+  if (flags && !on_device) CK(cudaStreamSynchronize(s), "limiter flags sync");
+  return ADER_OK;
+}
+
+ader_status ader_limiter_force(ader_ctx* c, const uint8_t* force) {
+  if (!c || !c->cfg.limiter) return ADER_ERR_ARG;
+  CK(cudaDeviceSynchronize(), "sync before limiter force");
+  if (!force) {
+    c->force_set = false;
+    return ADER_OK;
+  }
+  CK(cudaMemcpy(c->force, force, c->tree.cells.size(), cudaMemcpyHostToDevice), "upload force");
+  c->force_set = true;
   return ADER_OK;
 }
 

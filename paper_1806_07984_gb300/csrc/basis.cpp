@@ -40,10 +40,7 @@ ld lagrange(const ld* xi, int n, int j, ld x) {
   return v;
 }
 
-}  // namespace
-
-void make_basis(int n, BasisTables* out) {
-  ld xi[kMaxN], w[kMaxN];
+void gl_nodes(int n, ld* xi, ld* w) {
   const ld pi = 3.14159265358979323846264338327950288L;
   for (int i = 0; i < n; ++i) {
     ld x = std::cos(pi * (i + 0.75L) / (n + 0.5L));
@@ -60,6 +57,37 @@ void make_basis(int n, BasisTables* out) {
     xi[n - 1 - i] = 0.5L * (x + 1.0L);
     w[n - 1 - i] = 0.5L * 2.0L / ((1.0L - x * x) * dp * dp);
   }
+}
+
+// In-place Gauss-Jordan elimination with partial pivoting on [M | I]:
+// afterwards columns n..2n-1 hold M^-1.
+void gauss_jordan(ld (*A)[2 * kMaxN], int n) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (piv != c)
+      for (int j = 0; j < 2 * n; ++j) {
+        const ld t = A[c][j];
+        A[c][j] = A[piv][j];
+        A[piv][j] = t;
+      }
+    const ld inv = 1.0L / A[c][c];
+    for (int j = 0; j < 2 * n; ++j) A[c][j] *= inv;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const ld f = A[r][c];
+      if (f == 0.0L) continue;
+      for (int j = 0; j < 2 * n; ++j) A[r][j] -= f * A[c][j];
+    }
+  }
+}
+
+}  // namespace
+
+void make_basis(int n, BasisTables* out) {
+  ld xi[kMaxN], w[kMaxN];
+  gl_nodes(n, xi, w);
   ld lam[kMaxN];
   for (int j = 0; j < n; ++j) {
     lam[j] = 1.0L;
@@ -89,25 +117,7 @@ void make_basis(int n, BasisTables* out) {
       A[k][n + l] = (k == l) ? 1.0L : 0.0L;
     }
   }
-  for (int c = 0; c < n; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < n; ++r)
-      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
-    if (piv != c)
-      for (int j = 0; j < 2 * n; ++j) {
-        const ld t = A[c][j];
-        A[c][j] = A[piv][j];
-        A[piv][j] = t;
-      }
-    const ld inv = 1.0L / A[c][c];
-    for (int j = 0; j < 2 * n; ++j) A[c][j] *= inv;
-    for (int r = 0; r < n; ++r) {
-      if (r == c) continue;
-      const ld f = A[r][c];
-      if (f == 0.0L) continue;
-      for (int j = 0; j < 2 * n; ++j) A[r][j] -= f * A[c][j];
-    }
-  }
+  gauss_jordan(A, n);
   out->n = n;
   for (int i = 0; i < kMaxN; ++i) {
     out->xi[i] = out->w[i] = out->phi0[i] = out->phi1[i] = 0.0;
@@ -136,6 +146,42 @@ void make_basis(int n, BasisTables* out) {
       }
     }
   }
+}
+
+void make_subcells(int n, SubcellTables* out) {
+  ld xi[kMaxN], w[kMaxN];
+  gl_nodes(n, xi, w);
+  const int S = 2 * n - 1;
+  ld A[kMaxS][kMaxN];
+  for (int s = 0; s < S; ++s)
+    for (int j = 0; j < n; ++j) {
+      // mean of phi_j over [s/S, (s+1)/S]: n-point GL is exact for degree n-1
+      ld acc = 0.0L;
+      for (int q = 0; q < n; ++q) acc += w[q] * lagrange(xi, n, j, (s + xi[q]) / S);
+      A[s][j] = acc;
+    }
+  // R = (A^T A)^-1 A^T
+  ld G[kMaxN][2 * kMaxN];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      ld acc = 0.0L;
+      for (int s = 0; s < S; ++s) acc += A[s][i] * A[s][j];
+      G[i][j] = acc;
+      G[i][n + j] = (i == j) ? 1.0L : 0.0L;
+    }
+  gauss_jordan(G, n);
+  *out = SubcellTables{};
+  out->n = n;
+  out->S = S;
+  for (int s = 0; s < S; ++s)
+    for (int j = 0; j < n; ++j) out->A[s][j] = double(A[s][j]);
+  for (int i = 0; i < n; ++i)
+    for (int s = 0; s < S; ++s) {
+      ld acc = 0.0L;
+      for (int k = 0; k < n; ++k) acc += G[i][n + k] * A[s][k];
+      out->R[i][s] = double(acc);
+      out->Pi[i][s] = double(A[s][i] / (S * w[i]));
+    }
 }
 
 }  // namespace ader

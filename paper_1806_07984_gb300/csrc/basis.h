@@ -27,4 +27,20 @@ struct BasisTables {
 // Fills the tables for n = N + 1 nodes (1 <= n <= kMaxN).
 void make_basis(int n, BasisTables* out);
 
+constexpr int kMaxS = 2 * kMaxN - 1;  // subcells per direction, S = 2N + 1
+
+// Subcell operators of the a posteriori FV limiter (S = 2N + 1 equal
+// subintervals per direction):
+//   A[s][j]  mean of phi_j over [s/S, (s+1)/S]   (nodes -> subcell averages)
+//   R[i][s]  (A^T A)^-1 A^T                        (averages -> nodes, least squares)
+//   Pi[i][s] A[s][i] / (S w_i)                     (subface fluxes -> face nodes, L2)
+struct SubcellTables {
+  int n, S;
+  double A[kMaxS][kMaxN];
+  double R[kMaxN][kMaxS];
+  double Pi[kMaxN][kMaxS];
+};
+
+void make_subcells(int n, SubcellTables* out);
+
 }  // namespace ader

@@ -24,6 +24,14 @@ enum StatusBits : uint32_t {
   kStatusNonFiniteRate = 4u,
   kStatusBadTransfer = 8u,
   kStatusTensorTimeout = 16u,
+  kStatusLimiterTransition = 32u,
+};
+
+// Per-cell limiter flags of the last step.
+enum LimiterFlags : uint32_t {
+  kLimited = 1u,        // step redone by FV on the subcell patch
+  kFluxReplaced = 2u,   // unlimited, a face flux replaced by the FV subface fluxes
+  kKeptAtTransition = 4u,  // troubled, but a face is non-conforming: DG kept
 };
 
 struct PredictArgs {
@@ -92,6 +100,42 @@ struct TransferArgs {
   uint32_t* status;
   BasisTables B;
 };
+
+// A posteriori subcell FV limiter (Sec. 4, finite volumes as the limiter of
+// ADER-DG on (2N+1)^d subcell patches).
+struct LimiterArgs {
+  double* u;               // candidate state, overwritten with the final state
+  const double* u_old;     // u(T)
+  double* u_backup;        // bounds kernel: copy of u(T) written here
+  const double* ustar;     // u(T) + dt * volume term
+  double* fstar;           // face fluxes; unlimited neighbours of limited cells get FV fluxes
+  double* bounds;          // [c][var][2]: min, max of the subcell averages of u(T)
+  const int32_t* nbr;      // [c][2 * dir + side]: conforming neighbour or -1
+  const uint8_t* force;    // per cell, nonzero = treat as troubled (may be null)
+  uint32_t* flags;         // per cell LimiterFlags
+  int32_t* list;           // limited cells (counts[0] entries)
+  int32_t* fix_list;       // cells with replaced face fluxes (counts[1] entries)
+  int* counts;
+  const int8_t* level;
+  int64_t ncells;
+  const double* dt;
+  double gamma, delta0, eps;
+  unsigned long long* rate_max;
+  uint32_t* status;
+  double inv_h[kMaxLevels][3];
+  BasisTables B;
+  SubcellTables T;
+};
+
+enum class LimiterKernel { kBounds = 0, kDetect = 1, kFV = 2, kFix = 3 };
+
+// Limiter kernels exist for 2D orders 1..7 and 3D orders 1..5 (pde 0 Euler,
+// 1 acoustics); `grid` is the CTA count of the kFV and kFix kernels, which
+// loop over the device-side lists.
+cudaError_t launch_limiter_2d(int order, int pde, LimiterKernel which, const LimiterArgs& a, int grid,
+                              cudaStream_t s);
+cudaError_t launch_limiter_3d(int order, int pde, LimiterKernel which, const LimiterArgs& a, int grid,
+                              cudaStream_t s);
 
 enum class Precision { kFP64 = 0, kFP32 = 1, kTF32 = 2, kTF32x3 = 3, kBF16x3 = 4, kDF64 = 5 };
 

@@ -15,7 +15,8 @@ class Solver:
 
     def __init__(self, dim, order, pde="euler", base=(27, 27, 27), max_level=0, cfl=0.1,
                  gamma=1.4, picard_iters=0, precision="fp64", lo=(0.0, 0.0, 0.0),
-                 hi=(1.0, 1.0, 1.0), device=None, predictor="picard"):
+                 hi=(1.0, 1.0, 1.0), device=None, predictor="picard", limiter=False,
+                 limiter_delta0=1e-4, limiter_eps=1e-3):
         import torch
         self.torch = torch
         self.device = torch.device("cuda" if device is None else device)
@@ -34,6 +35,9 @@ class Solver:
         cfg.picard_iters = picard_iters
         cfg.prec = A.PRECISIONS[precision]
         cfg.predictor = A.ADER_PREDICTOR_CK if predictor == "ck" else A.ADER_PREDICTOR_PICARD
+        cfg.limiter = 1 if limiter else 0
+        cfg.limiter_delta0 = limiter_delta0
+        cfg.limiter_eps = limiter_eps
         self.cfg = cfg
         self.dim, self.order, self.n, self.nvar = dim, order, order + 1, cfg.nvar
         with torch.cuda.device(self.device):
@@ -145,6 +149,17 @@ class Solver:
 
     def launch_count(self):
         return A.ader_launch_count(self.ctx)
+
+    # --------------------------------------------------------------- limiter
+    def limiter_flags(self):
+        """(flags per cell, number of limited cells) of the last corrector:
+        bit 0 limited, bit 1 face flux replaced, bit 2 kept at a transition."""
+        return A.ader_limiter_flags(self.ctx, self._stream(None))
+
+    def force_limit(self, mask):
+        """Treat the cells in ``mask`` as troubled in the following steps
+        (None clears)."""
+        A.ader_limiter_force(self.ctx, mask)
 
     def close(self):
         if getattr(self, "ctx", None):

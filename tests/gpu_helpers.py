@@ -21,11 +21,12 @@ def lib_keys(solver):
 
 
 def build_pair(dim, order, pde="euler", base=9, max_level=0, centers=(), radius=0.15,
-               precision="fp64", picard_iters=0, cfl=None, predictor="picard"):
+               precision="fp64", picard_iters=0, cfl=None, predictor="picard", **solver_kw):
     from paper_1806_07984_gb300 import Solver
     solver = Solver(dim, order, pde, base=(base,) * 3, max_level=max_level,
                     cfl=workloads.ADER_CFL[order] if cfl is None else cfl,
-                    precision=precision, picard_iters=picard_iters, predictor=predictor)
+                    precision=precision, picard_iters=picard_iters, predictor=predictor,
+                    **solver_kw)
     om = omesh.Mesh(dim, (base,) * dim, max_level)
     B1 = obasis.Basis(1)
     for c in centers:

@@ -1,0 +1,114 @@
+"""GPU parity of the a posteriori subcell FV limiter against the oracle:
+forced limiting (all cells, a seeded subset, at a resolution transition),
+detection on a circular explosion over several steps, flags, conservation
+and the next time step."""
+import numpy as np
+import pytest
+
+from oracle import ader as oader, basis as obasis, limiter as olim, pde as opde
+from gpu_helpers import build_pair, rel_l2
+from oracle_helpers import random_state
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def flags_of(out):
+    f = np.zeros(len(out.limited), dtype=np.uint32)
+    f |= out.limited.astype(np.uint32)
+    f |= 2 * out.fixed.astype(np.uint32)
+    f |= 4 * out.kept.astype(np.uint32)
+    return f
+
+
+def limited_step_parity(solver, om, perm, u0, P, B, force=None, steps=1):
+    """Run `steps` limited steps on both sides; compare state, flags, dt."""
+    h = om.cell_widths()
+    dt = oader.cfl_dt(u0, h, P, B.order)
+    u = u0
+    solver.set_state(u0[perm])
+    solver.set_dt(dt)
+    if force is not None:
+        solver.force_limit(force[perm])
+    outs = []
+    for _ in range(steps):
+        ref = olim.step_limited(om, u, dt, P, B, force=force)
+        solver.step(1)
+        got = solver.get_state().cpu().numpy()
+        flags, nlim = solver.limiter_flags()
+        assert np.array_equal(flags, flags_of(ref)[perm])
+        assert nlim == int(ref.limited.sum())
+        assert rel_l2(got, ref.u[perm]) < TOL
+        assert rel_l2(got - u[perm], ref.u[perm] - u[perm]) < 1e-9
+        assert abs(solver.dt.item() - ref.dt_next) < TOL * ref.dt_next
+        outs.append(ref)
+        u, dt = ref.u, ref.dt_next
+    return outs
+
+
+@pytest.mark.parametrize("dim,order,base", [(2, 3, 4), (2, 7, 3), (3, 2, 3), (3, 5, 3)])
+def test_all_cells_limited(dim, order, base):
+    solver, om, perm = build_pair(dim, order, "euler", base, 0, limiter=True)
+    B = obasis.Basis(order)
+    P = opde.make_pde("euler", dim)
+    u0 = random_state(om, B, "euler", seed=40 + order)
+    force = np.ones(len(om.cells), dtype=bool)
+    limited_step_parity(solver, om, perm, u0, P, B, force)
+    assert solver.status() == 0
+
+
+@pytest.mark.parametrize("dim,order,base,pde", [(2, 3, 6, "euler"), (3, 3, 3, "euler"),
+                                                (3, 5, 3, "euler"), (2, 4, 5, "acoustics"),
+                                                (3, 2, 3, "acoustics")])
+def test_forced_subset_conserves(dim, order, base, pde):
+    solver, om, perm = build_pair(dim, order, pde, base, 0, limiter=True)
+    B = obasis.Basis(order)
+    P = opde.make_pde(pde, dim)
+    u0 = random_state(om, B, pde, seed=50 + order)
+    force = np.random.default_rng(order).random(len(om.cells)) < 0.3
+    outs = limited_step_parity(solver, om, perm, u0, P, B, force, steps=2)
+    assert outs[0].fixed.any()
+    h = om.cell_widths()
+    inv = np.argsort(perm)
+    got = solver.get_state().cpu().numpy()[inv]
+    I0 = oader.cell_integral(u0, h, B)
+    assert np.allclose(oader.cell_integral(got, h, B), I0, atol=1e-12, rtol=0)
+
+
+def test_transition_cells_keep_dg():
+    solver, om, perm = build_pair(2, 3, "euler", 9, 1, centers=[(0.5, 0.5)], radius=0.1,
+                                  limiter=True)
+    B = obasis.Basis(3)
+    P = opde.Euler(2)
+    u0 = random_state(om, B, "euler", seed=7)
+    nb = olim.neighbors(om)
+    at_tr = ~(nb >= 0).all(axis=(1, 2))
+    force = np.zeros(len(om.cells), dtype=bool)
+    force[np.flatnonzero(at_tr)[:3]] = True
+    force[np.flatnonzero(~at_tr)[::7]] = True
+    outs = limited_step_parity(solver, om, perm, u0, P, B, force)
+    assert outs[0].kept[force & at_tr].all() and outs[0].limited[force & ~at_tr].all()
+    assert solver.status() == 32          # reported, and the step is otherwise clean
+
+
+@pytest.mark.parametrize("dim,order,base,steps", [(2, 3, 27, 3), (3, 2, 9, 1)])
+def test_explosion_detection(dim, order, base, steps):
+    solver, om, perm = build_pair(dim, order, "euler", base, 0, limiter=True)
+    B = obasis.Basis(order)
+    P = opde.Euler(dim)
+    X = om.node_coords(B.xi)
+    u0 = np.ascontiguousarray(np.moveaxis(workloads.circular_explosion(X, width=0.02), 0, 1))
+    outs = limited_step_parity(solver, om, perm, u0, P, B, steps=steps)
+    assert all(0 < o.limited.sum() < len(om.cells) // 2 for o in outs)
+    assert solver.status() == 0
+
+
+def test_limiter_off_by_default_and_guarded():
+    from paper_1806_07984_gb300 import Solver, ader as A
+    s = Solver(2, 3, "euler", base=(3, 3, 1), cfl=workloads.ADER_CFL[3])
+    with pytest.raises(A.AderError):
+        s.limiter_flags()
+    with pytest.raises(A.AderError):
+        Solver(3, 6, "euler", base=(3, 3, 3), cfl=workloads.ADER_CFL[6], limiter=True)

@@ -111,3 +111,20 @@ def test_mesh_bad_arguments(A):
         A.ader_mesh_create(4, (3, 3, 3), 1)
     with pytest.raises(A.AderError):
         A.ader_mesh_create(2, (0, 3, 1), 1)
+
+
+def test_config_rejected_before_any_device_call(A):
+    """ader_init validates the configuration on the host: unsupported limiter
+    orders and malformed limiter flags return ADER_ERR_ARG without a GPU."""
+    def cfg(dim, order, limiter):
+        c = A.ader_config()
+        c.dim, c.order, c.nvar, c.pde = dim, order, dim + 2, A.ADER_EULER
+        c.gamma, c.cfl = 1.4, 0.05
+        for d in range(3):
+            c.base[d], c.lo[d], c.hi[d] = 3, 0.0, 1.0
+        c.limiter = limiter
+        return c
+    for bad in (cfg(3, 6, 1), cfg(3, 7, 1), cfg(2, 3, 2)):
+        with pytest.raises(A.AderError) as e:
+            A.ader_init(bad)
+        assert e.value.status == -1
