@@ -323,6 +323,45 @@ def run_adjoint(torch, predictor="picard"):
             "dofs": dofs}
 
 
+def run_limiter(torch, dim=2, order=3, base=729, steps=10, warmup=2):
+    """Circular explosion (a density and pressure jump, smoothed over half a
+    cell) on a uniform periodic grid with the a posteriori subcell FV limiter;
+    DoF-updates/s with and without the limiter on the same run."""
+    from paper_1806_07984_gb300 import Solver
+    out = {}
+    for lim in (True, False):
+        s = Solver(dim, order, "euler", base=(base,) * 3, cfl=workloads.ADER_CFL[order], limiter=lim)
+        X = s.node_coords()
+        u0 = np.ascontiguousarray(np.moveaxis(
+            workloads.circular_explosion(X, width=0.5 / base), 0, 1))
+        del X
+        s.set_state(torch.from_numpy(u0).cuda())
+        s.compute_dt()
+        s.step(warmup)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        dofs = s.ncells * s.nvar * s.n ** dim
+        rec = {"value": dofs * steps / sec, "unit": "DoF-updates/s", "ms_per_step": sec / steps * 1e3,
+               "status": s.status()}
+        if lim:
+            flags, nlim = s.limiter_flags()
+            rec["limited_cells_last_step"] = int(nlim)
+            rec["limited_fraction"] = nlim / s.ncells
+            rec["flux_replaced_cells"] = int(((flags & 2) != 0).sum())
+        out["limiter" if lim else "no_limiter"] = rec
+        s.close()
+    out["workload"] = (f"{dim}D Euler N={order}, {base}^{dim} periodic, circular explosion "
+                       f"(rho 1/0.125, p 1/0.1, r=0.25), {steps} steps after {warmup}")
+    out["overhead"] = out["no_limiter"]["value"] / out["limiter"]["value"]
+    return out
+
+
 def time_predictor(s, torch, reps=3):
     """Average duration of one ader_predict(ADER_ALL) launch, CUDA events on
     the launching stream."""
@@ -426,6 +465,7 @@ def main():
                     help="predictor precisions compared with FP64 ('' to skip)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-limiter", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -562,6 +602,8 @@ def main():
 
     adjoint = ({"picard": run_adjoint(torch, "picard"), "ck": run_adjoint(torch, "ck")}
                if (not args.no_adjoint and world == 1) else None)
+    limiter = ({"2d_n3_729": run_limiter(torch, 2, 3, 729), "3d_n5_27": run_limiter(torch, 3, 5, 27, 5)}
+               if (not args.no_limiter and world == 1) else None)
 
     # ---- end to end through the public API with host buffers ---------------
     # Every step: H2D of the state from pinned host memory, one step, D2H of
@@ -609,7 +651,7 @@ def main():
                        "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
                        "remesh_every": wl["remesh_every"]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
-            "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint}
+            "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
     if rank == 0:

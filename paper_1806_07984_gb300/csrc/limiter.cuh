@@ -37,6 +37,8 @@ struct LimShape {
   static constexpr int SS = ipow(S, DIM);     // subcells
   static constexpr int SF = ipow(S, DIM - 1);  // subfaces of one face
   static constexpr int THREADS = 256;
+  // bounds / detection: one CTA per cell, about one thread per subcell
+  static constexpr int CELL_THREADS = SS <= 64 ? 64 : (SS <= 128 ? 128 : 256);
 };
 
 // Stage the 1D tables in shared memory (dynamic indices stay out of the
@@ -133,10 +135,11 @@ __global__ void __launch_bounds__(256) limiter_bounds_kernel(const LimiterArgs a
   constexpr int n = L::n, S = L::S, NS = L::NS, SS = L::SS, M = PDE::M;
   extern __shared__ double smem[];
   double* sA = smem;
-  double* red = sA + S * n;
-  double* U = red + 32;
+  double* red = sA + S * n;  // [warp][min M | max M]
+  double* U = red + 16 * M;
   double* X = U + M * NS;
   const int64_t cell = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   load_tables<N>(a.T, sA, nullptr, nullptr);
   for (int t = threadIdx.x; t < M * NS; t += blockDim.x) {
     const double x = a.u[cell * M * NS + t];
@@ -145,20 +148,40 @@ __global__ void __launch_bounds__(256) limiter_bounds_kernel(const LimiterArgs a
   }
   __syncthreads();
   const double* P = subcell_partial<DIM, N, M>(U, sA, X);
+  double mn[M], mx[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    double mn = INFINITY, mx = -INFINITY;
-    for (int sub = threadIdx.x; sub < SS; sub += blockDim.x) {
+    mn[v] = INFINITY;
+    mx[v] = -INFINITY;
+  }
+  for (int sub = threadIdx.x; sub < SS; sub += blockDim.x)
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
       const double x = sub_value<DIM, N, M>(P, sA, v, sub);
-      mn = fmin(mn, x);
-      mx = fmax(mx, x);
+      mn[v] = fmin(mn[v], x);
+      mx[v] = fmax(mx[v], x);
     }
-    mn = block_reduce(mn, false, red);
-    mx = block_reduce(mx, true, red);
-    if (threadIdx.x == 0) {
-      a.bounds[(cell * M + v) * 2 + 0] = mn;
-      a.bounds[(cell * M + v) * 2 + 1] = mx;
+#pragma unroll
+  for (int v = 0; v < M; ++v)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[v] = fmin(mn[v], __shfl_xor_sync(0xffffffffu, mn[v], o));
+      mx[v] = fmax(mx[v], __shfl_xor_sync(0xffffffffu, mx[v], o));
     }
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      red[warp * 2 * M + v] = mn[v];
+      red[warp * 2 * M + M + v] = mx[v];
+    }
+  __syncthreads();
+  if (threadIdx.x < 2 * M) {
+    const int v = threadIdx.x % M;
+    const bool is_max = threadIdx.x >= M;
+    double x = red[threadIdx.x];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w)
+      x = is_max ? fmax(x, red[w * 2 * M + threadIdx.x]) : fmin(x, red[w * 2 * M + threadIdx.x]);
+    a.bounds[(cell * M + v) * 2 + (is_max ? 1 : 0)] = x;
   }
 }
 
@@ -516,16 +539,16 @@ cudaError_t launch_limiter_t(LimiterKernel which, const LimiterArgs& a, int grid
   constexpr int M = PDE::M, n = L::n, S = L::S;
   if (which == LimiterKernel::kBounds || which == LimiterKernel::kDetect) {
     if (a.ncells == 0) return cudaSuccess;
-    const size_t bytes = sizeof(double) * size_t(S * n + 32 + 2 * M + M * L::NS +
+    const size_t bytes = sizeof(double) * size_t(S * n + 16 * M + M * L::NS +
                                                  M * partial_scratch<DIM, N>());
     if (which == LimiterKernel::kBounds) {
       auto k = limiter_bounds_kernel<DIM, N, PDE>;
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      k<<<unsigned(a.ncells), L::THREADS, bytes, s>>>(a);
+      k<<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
     } else {
       auto k = limiter_detect_kernel<DIM, N, PDE>;
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      k<<<unsigned(a.ncells), L::THREADS, bytes, s>>>(a);
+      k<<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
     }
   } else if (which == LimiterKernel::kFV) {
     const size_t bytes = sizeof(double) * size_t(FvSmem<DIM, N, M>::doubles);
