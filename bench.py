@@ -146,11 +146,16 @@ class ClockSampler:
 _U0_CACHE = {}
 
 
+PIPELINE_CHUNKS = 0   # ader_step enclave chunks (0 = the library default)
+PIPELINE_CTAS = 0     # CTAs per SM of the overlapping face/corrector kernels (0 = default)
+
+
 def build_problem(wl, precision, device):
     from paper_1806_07984_gb300 import Solver
     dim, order = wl["dim"], wl["order"]
     s = Solver(dim, order, "euler", base=(wl["base"],) * 3, max_level=wl["max_level"],
-               cfl=workloads.ADER_CFL[order], precision=precision, device=device)
+               cfl=workloads.ADER_CFL[order], precision=precision, device=device,
+               pipeline_chunks=PIPELINE_CHUNKS, pipeline_ctas=PIPELINE_CTAS)
     center = workloads.sphere_center(0.0)[:dim]
     for _ in range(wl["max_level"]):
         s.remesh(s.sphere_flags(center, wl["radius"]))
@@ -466,7 +471,14 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-limiter", action="store_true")
+    ap.add_argument("--pipeline", type=int, default=0,
+                    help="enclave chunks per step (0 = library default, 1 = no pipelining)")
+    ap.add_argument("--pipeline-ctas", type=int, default=0,
+                    help="CTAs per SM of the face/corrector kernels that overlap the predictor")
     args = ap.parse_args()
+    global PIPELINE_CHUNKS, PIPELINE_CTAS
+    PIPELINE_CHUNKS = args.pipeline
+    PIPELINE_CTAS = args.pipeline_ctas
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         reference_arm(args, args.workload, wl)
@@ -649,7 +661,9 @@ def main():
                        "cells": ncells, "dofs": dofs_now, "precision": args.precision,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
-                       "remesh_every": wl["remesh_every"]},
+                       "remesh_every": wl["remesh_every"],
+                       "pipeline_chunks": args.pipeline or 8,
+                       "pipeline_ctas_per_sm": args.pipeline_ctas or 1},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
             "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -119,6 +119,8 @@ typedef struct {
                                 (2D orders 1..7, 3D orders 1..5); see ader_limiter_flags */
   double limiter_delta0;     /* relaxed maximum principle: delta = max(delta0, eps (max - min)); */
   double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
+  int pipeline_chunks;       /* ader_step: enclave chunks K (0 selects 8, 1 disables); see ader_step */
+  int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 1) */
 } ader_config;
 
 typedef struct ader_ctx ader_ctx;
@@ -204,7 +206,15 @@ ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_de
  * high-priority stream, the enclave predictor on its low-priority stream, then
  * the remaining faces and the corrector after both; the step's dt is read from
  * *dt_dev and the next dt written back to it.  Ordered after earlier work on
- * `stream`; later work on `stream` sees the result. */
+ * `stream`; later work on `stream` sees the result.
+ * With cfg.pipeline_chunks K > 1 the enclave predictor runs as K chunks of
+ * contiguous cells on the low-priority stream, and after chunk k the
+ * high-priority stream solves the faces whose two cells are then predicted
+ * and corrects the cells whose faces are then all solved, so the face and
+ * corrector work (FP64) overlaps the remaining predictor chunks.  Those face
+ * and corrector kernels are capped at cfg.pipeline_ctas CTAs per SM (striding
+ * over their items) so that they share the SMs with predictor CTAs instead of
+ * taking them over.  The result does not depend on K or the cap. */
 ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
 
 /* Dynamic adaptivity (Sec. 2.3): flags per cell in mesh order (+1 refine,

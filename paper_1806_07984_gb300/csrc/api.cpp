@@ -28,6 +28,8 @@ struct ader_ctx {
   double *u = nullptr, *ustar = nullptr, *faceQ = nullptr, *faceF = nullptr, *fstar = nullptr;
   int8_t* level = nullptr;
   int32_t *all_cells = nullptr, *skel_cells = nullptr, *encl_cells = nullptr;
+  int32_t* corr_cells = nullptr;         // cells grouped by pipeline stage (Tree::corr_cells)
+  std::vector<cudaEvent_t> ev_chunk;     // one per enclave chunk
   ConfFace* conf = nullptr;
   int64_t conf_cap = 0;
   ParentFace* parents = nullptr;
@@ -144,9 +146,10 @@ ader_status ensure_cells(ader_ctx* c, int64_t need) {
   cudaFree(c->all_cells);
   cudaFree(c->skel_cells);
   cudaFree(c->encl_cells);
+  cudaFree(c->corr_cells);
   c->ustar = c->faceQ = c->faceF = c->fstar = nullptr;
   c->level = nullptr;
-  c->all_cells = c->skel_cells = c->encl_cells = nullptr;
+  c->all_cells = c->skel_cells = c->encl_cells = c->corr_cells = nullptr;
   CK(cudaMalloc(&c->ustar, cell_bytes * size_t(nc)), "cudaMalloc ustar");
   CK(cudaMalloc(&c->faceQ, face_bytes * size_t(nc)), "cudaMalloc faceQ");
   CK(cudaMalloc(&c->faceF, face_bytes * size_t(nc)), "cudaMalloc faceF");
@@ -155,6 +158,7 @@ ader_status ensure_cells(ader_ctx* c, int64_t need) {
   CK(cudaMalloc(&c->all_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
   CK(cudaMalloc(&c->skel_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
   CK(cudaMalloc(&c->encl_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
+  CK(cudaMalloc(&c->corr_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
   if (c->cfg.limiter) {
     for (void* p : {(void*)c->u_old, (void*)c->bounds, (void*)c->lim_flags, (void*)c->lim_list,
                     (void*)c->fix_list, (void*)c->nbr, (void*)c->force})
@@ -199,6 +203,9 @@ ader_status upload_mesh(ader_ctx* c) {
   if (!t.encl_cells.empty())
     CK(cudaMemcpy(c->encl_cells, t.encl_cells.data(), sizeof(int32_t) * t.encl_cells.size(),
                   cudaMemcpyHostToDevice), "upload enclave");
+  if (!t.corr_cells.empty())
+    CK(cudaMemcpy(c->corr_cells, t.corr_cells.data(), sizeof(int32_t) * t.corr_cells.size(),
+                  cudaMemcpyHostToDevice), "upload corrector groups");
   CK(grow(&c->conf, &c->conf_cap, int64_t(t.conf.size())), "cudaMalloc conf");
   if (!t.conf.empty())
     CK(cudaMemcpy(c->conf, t.conf.data(), sizeof(ConfFace) * t.conf.size(), cudaMemcpyHostToDevice),
@@ -349,32 +356,52 @@ cudaError_t do_limiter(ader_ctx* c, LimiterKernel which, const LimiterArgs& a, i
                          : launch_limiter_3d(c->cfg.order, pde, which, a, grid, s);
 }
 
-ader_status enqueue_correct(ader_ctx* c, const double* dt, double* dt_next, cudaStream_t s) {
+// Corrector arguments for a stage: the cell list (null = all cells), and in
+// limiter mode the candidate's rate and status words.
+CorrectArgs stage_correct_args(ader_ctx* c, const double* dt, const int32_t* cells, int64_t count) {
   CorrectArgs a = correct_args(c, dt);
-  if (!c->cfg.limiter) {
-    CK(do_correct(c, true, a, s), "corrector");
-    c->launches += 1;
-    CK(launch_finalize_dt(c->rate, c->cfg.cfl, dt_next, c->status, s), "finalize dt");
-    return ADER_OK;
+  a.cells = cells;
+  if (cells) a.ncells = count;
+  if (c->cfg.limiter) {
+    a.rate_max = c->rate_cand;
+    a.status = c->status_cand;
   }
-  // limiter mode: bounds of u(T) and its backup, the candidate, detection,
-  // FV on the limited cells, the neighbours' corrector with FV face fluxes,
-  // then the CFL rate of the final state
-  const LimiterArgs la = limiter_args(c, dt);
-  const int grid = 2 * c->num_sms;
-  CK(do_limiter(c, LimiterKernel::kBounds, la, grid, s), "limiter bounds");
-  a.rate_max = c->rate_cand;
-  a.status = c->status_cand;
-  CK(do_correct(c, true, a, s), "candidate corrector");
-  CK(cudaMemsetAsync(c->lim_counts, 0, 2 * sizeof(int), s), "clear limiter counts");
-  CK(do_limiter(c, LimiterKernel::kDetect, la, grid, s), "limiter detection");
-  CK(do_limiter(c, LimiterKernel::kFV, la, grid, s), "limiter FV step");
-  CK(do_limiter(c, LimiterKernel::kFix, la, grid, s), "limiter neighbour correction");
-  CorrectArgs r = correct_args(c, dt);
-  CK(do_correct(c, false, r, s), "CFL rate");
+  return a;
+}
+
+// Limiter mode, before the first corrector of a step overwrites u(T): its
+// backup and the subcell bounds.
+ader_status enqueue_limiter_bounds(ader_ctx* c, const double* dt, cudaStream_t s) {
+  CK(do_limiter(c, LimiterKernel::kBounds, limiter_args(c, dt), 2 * c->num_sms, s), "limiter bounds");
+  return ADER_OK;
+}
+
+// After all correctors of a step: in limiter mode detection, FV on the
+// limited cells, the neighbours' corrector with FV face fluxes and the CFL
+// rate of the final state; then dt_next.
+ader_status enqueue_finish(ader_ctx* c, const double* dt, double* dt_next, cudaStream_t s) {
+  if (c->cfg.limiter) {
+    const LimiterArgs la = limiter_args(c, dt);
+    const int grid = 2 * c->num_sms;
+    CK(cudaMemsetAsync(c->lim_counts, 0, 2 * sizeof(int), s), "clear limiter counts");
+    CK(do_limiter(c, LimiterKernel::kDetect, la, grid, s), "limiter detection");
+    CK(do_limiter(c, LimiterKernel::kFV, la, grid, s), "limiter FV step");
+    CK(do_limiter(c, LimiterKernel::kFix, la, grid, s), "limiter neighbour correction");
+    CorrectArgs r = correct_args(c, dt);
+    CK(do_correct(c, false, r, s), "CFL rate");
+  }
   c->launches += 1;
   CK(launch_finalize_dt(c->rate, c->cfg.cfl, dt_next, c->status, s), "finalize dt");
   return ADER_OK;
+}
+
+ader_status enqueue_correct(ader_ctx* c, const double* dt, double* dt_next, cudaStream_t s) {
+  if (c->cfg.limiter) {
+    ader_status st = enqueue_limiter_bounds(c, dt, s);
+    if (st != ADER_OK) return st;
+  }
+  CK(do_correct(c, true, stage_correct_args(c, dt, nullptr, 0), s), "corrector");
+  return enqueue_finish(c, dt, dt_next, s);
 }
 
 bool valid_config(const ader_config* cfg, std::string* why) {
@@ -402,6 +429,10 @@ bool valid_config(const ader_config* cfg, std::string* why) {
   if (cfg->predictor == ADER_PREDICTOR_CK && (cfg->pde != ADER_ACOUSTICS || cfg->prec > ADER_FP32))
     return *why = "Cauchy-Kowalevski predictor: linear acoustics, FP64 or FP32", false;
   if (cfg->limiter != 0 && cfg->limiter != 1) return *why = "limiter must be 0 or 1", false;
+  if (cfg->pipeline_chunks < 0 || cfg->pipeline_chunks > 64)
+    return *why = "pipeline_chunks must be in 0..64", false;
+  if (cfg->pipeline_ctas < 0 || cfg->pipeline_ctas > 32)
+    return *why = "pipeline_ctas must be in 0..32", false;
   if (cfg->limiter && cfg->dim == 3 && cfg->order > 5)
     return *why = "subcell limiter: 3D orders 1..5", false;
   return true;
@@ -454,6 +485,7 @@ ader_status ader_init(const ader_config* cfg, ader_ctx** out) {
     delete c;
     return ADER_ERR_MESH;
   }
+  c->tree.set_chunks(cfg->pipeline_chunks == 0 ? 8 : cfg->pipeline_chunks);
   ader_status st = ADER_OK;
   auto fail = [&](ader_status s) {
     ader_destroy(c);
@@ -507,8 +539,10 @@ void ader_destroy(ader_ctx* c) {
                   (void*)c->status, (void*)c->dt_scratch, (void*)c->u_old, (void*)c->bounds,
                   (void*)c->lim_flags, (void*)c->lim_list, (void*)c->fix_list, (void*)c->nbr,
                   (void*)c->force, (void*)c->lim_counts, (void*)c->rate_cand,
-                  (void*)c->status_cand})
+                  (void*)c->status_cand, (void*)c->corr_cells})
     if (p) cudaFree(p);
+  for (cudaEvent_t e : c->ev_chunk)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : {c->ev_begin, c->ev_step, c->ev_lo, c->ev_end})
     if (e) cudaEventDestroy(e);
   if (c->s_hi) cudaStreamDestroy(c->s_hi);
@@ -614,12 +648,71 @@ ader_status ader_correct(ader_ctx* c, const double* dt_dev, double* dt_next_dev,
   return enqueue_correct(c, dt_dev, dt_next_dev, static_cast<cudaStream_t>(stream));
 }
 
+// One step with the enclave predictor in K chunks: after chunk k the
+// high-priority stream solves the faces completed by it and corrects the
+// cells whose faces are then all solved (Tree::set_chunks).
+ader_status step_pipelined(ader_ctx* c, double* dt_dev) {
+  const Tree& t = c->tree;
+  const int K = t.chunks;
+  while (int(c->ev_chunk.size()) < K) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    c->ev_chunk.push_back(e);
+  }
+  CK(cudaEventRecord(c->ev_step, c->s_hi), "event");
+  CK(cudaStreamWaitEvent(c->s_lo, c->ev_step, 0), "event");
+  if (c->cfg.limiter) {
+    ader_status st = enqueue_limiter_bounds(c, dt_dev, c->s_hi);
+    if (st != ADER_OK) return st;
+  }
+  PredictArgs ps = predict_args(c, dt_dev, ADER_SKELETON);
+  CK(do_predict(c, ps, c->s_hi), "skeleton predictor");
+  ader_status st = enqueue_riemann(c, ADER_SKELETON, c->s_hi);
+  if (st != ADER_OK) return st;
+  const int cap = c->num_sms * (c->cfg.pipeline_ctas > 0 ? c->cfg.pipeline_ctas : 1);
+  auto correct_group = [&](int g) -> ader_status {
+    const int64_t b = t.corr_off[size_t(g)], e = t.corr_off[size_t(g) + 1];
+    if (e > b) {
+      CorrectArgs ca = stage_correct_args(c, dt_dev, c->corr_cells + b, e - b);
+      ca.max_ctas = cap;
+      CK(do_correct(c, true, ca, c->s_hi), "corrector");
+    }
+    return ADER_OK;
+  };
+  st = correct_group(0);
+  if (st != ADER_OK) return st;
+  for (int k = 0; k < K; ++k) {
+    PredictArgs pe = predict_args(c, dt_dev, ADER_ENCLAVE);
+    pe.cells = c->encl_cells + t.chunk_off[size_t(k)];
+    pe.count = t.chunk_off[size_t(k) + 1] - t.chunk_off[size_t(k)];
+    CK(do_predict(c, pe, c->s_lo), "enclave predictor");
+    CK(cudaEventRecord(c->ev_chunk[size_t(k)], c->s_lo), "event");
+  }
+  for (int k = 0; k < K; ++k) {
+    CK(cudaStreamWaitEvent(c->s_hi, c->ev_chunk[size_t(k)], 0), "event");
+    RiemannArgs a = riemann_args(c);
+    a.conf = c->conf + t.n_conf_skeleton + t.face_off[size_t(k)];
+    a.nconf = t.face_off[size_t(k) + 1] - t.face_off[size_t(k)];
+    a.nparents = 0;
+    a.max_ctas = cap;
+    CK(do_faces(c, 0, a, c->s_hi), "riemann conforming faces");
+    st = correct_group(k + 1);
+    if (st != ADER_OK) return st;
+  }
+  return enqueue_finish(c, dt_dev, dt_dev, c->s_hi);
+}
+
 ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
   if (!c || !dt_dev || nsteps < 0) return ADER_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaEventRecord(c->ev_begin, s), "event");
   CK(cudaStreamWaitEvent(c->s_hi, c->ev_begin, 0), "event");
   for (int k = 0; k < nsteps; ++k) {
+    if (c->tree.chunks > 1) {
+      ader_status st = step_pipelined(c, dt_dev);
+      if (st != ADER_OK) return st;
+      continue;
+    }
     CK(cudaEventRecord(c->ev_step, c->s_hi), "event");
     CK(cudaStreamWaitEvent(c->s_lo, c->ev_step, 0), "event");
     PredictArgs ps = predict_args(c, dt_dev, ADER_SKELETON);

@@ -45,11 +45,20 @@ __device__ __forceinline__ void rusanov_store(const double (&QL)[PDE::M], const 
 }
 
 template <int DIM, int N, class PDE>
+__device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t f, int lane);
+
+// One warp per face; a grid smaller than the face count strides over them.
+template <int DIM, int N, class PDE>
 __global__ void riemann_conf_kernel(const RiemannArgs a) {
-  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M, PER = (NF + 31) / 32;
   const int lane = threadIdx.x & 31;
-  const int64_t f = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (f >= a.nconf) return;
+  const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t f = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; f < a.nconf; f += warps)
+    riemann_conf_face<DIM, N, PDE>(a, f, lane);
+}
+
+template <int DIM, int N, class PDE>
+__device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t f, int lane) {
+  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M, PER = (NF + 31) / 32;
   const ConfFace cf = a.conf[f];
   const int d = cf.dir;
   const int64_t oL = (int64_t(cf.left) * 2 * DIM + 2 * d + 1) * M * NF;
@@ -280,15 +289,16 @@ __device__ __forceinline__ void lift_node(const double* ustar, const double* fst
 template <int DIM, int N, class PDE, bool UPDATE>
 __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) correct_kernel(const CorrectArgs a) {
   using SH = PredictShape<DIM, N>;
-  constexpr int n = SH::n, NS = SH::NS, NF = SH::NF, CPB = SH::CPB, M = PDE::M;
+  constexpr int NS = SH::NS, CPB = SH::CPB, M = PDE::M;
   const int tid = threadIdx.x;
   const int cl = tid / NS;
   const int node = tid - cl * NS;
-  const int64_t cell = int64_t(blockIdx.x) * CPB + cl;
-  const bool valid = cell < a.ncells;
+  const int64_t nblk = (a.ncells + CPB - 1) / CPB;
   double rate = 0.0;
-  if (valid) {
-    const int id[3] = {node % n, (node / n) % n, node / (n * n)};
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t idx = blk * CPB + cl;
+    if (idx >= a.ncells || node >= NS) continue;
+    const int64_t cell = a.cells ? int64_t(a.cells[idx]) : idx;
     const int lv = int(a.level[cell]);
     double q[M];
     if (UPDATE) {
@@ -299,16 +309,15 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) correct_kernel(
       for (int v = 0; v < M; ++v) q[v] = a.u[(cell * M + v) * NS + node];
     }
     bool ok_all = true;
+    double r = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       bool ok;
-      rate += PDE::max_speed(q, d, a.gamma, &ok) * a.inv_h[lv][d];
+      r += PDE::max_speed(q, d, a.gamma, &ok) * a.inv_h[lv][d];
       ok_all = ok_all && ok;
     }
-    if (!ok_all) {
-      atomicOr(a.status, kStatusNonPhysical);
-      rate = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks the rate
-    }
+    if (!ok_all) atomicOr(a.status, kStatusNonPhysical);
+    rate = fmax(rate, r);
   }
   block_max_to(rate, a.rate_max);
 }
@@ -427,7 +436,8 @@ cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
   const int threads = 128;
   int64_t items = which == 0 ? a.nconf : (which == 1 ? a.nparents * S : a.nparents);
   if (items == 0) return cudaSuccess;
-  const int64_t blocks = (items * 32 + threads - 1) / threads;
+  int64_t blocks = (items * 32 + threads - 1) / threads;
+  if (which == 0 && a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
   if (which == 0)
     riemann_conf_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
   else if (which == 1)
@@ -441,7 +451,8 @@ template <int DIM, int N, class PDE, bool UPDATE>
 cudaError_t launch_correct_t(const CorrectArgs& a, cudaStream_t s) {
   using SH = PredictShape<DIM, N>;
   if (a.ncells == 0) return cudaSuccess;
-  const int64_t blocks = (a.ncells + SH::CPB - 1) / SH::CPB;
+  int64_t blocks = (a.ncells + SH::CPB - 1) / SH::CPB;
+  if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
   correct_kernel<DIM, N, PDE, UPDATE><<<unsigned(blocks), SH::THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -61,6 +61,7 @@ struct RiemannArgs {
   int64_t nparents;
   double gamma;
   uint32_t* status;
+  int max_ctas;               // conforming faces: at most this many CTAs (0 = one warp per face)
   BasisTables B;
 };
 
@@ -69,11 +70,13 @@ struct CorrectArgs {
   const double* fstar;
   double* u;
   const int8_t* level;
+  const int32_t* cells;  // cells to process (ncells entries), or null for 0..ncells-1
   int64_t ncells;
   const double* dt;
   unsigned long long* rate_max;  // max over nodes of sum_d lambda_d / h_d (as FP64 bits)
   double gamma;
   uint32_t* status;
+  int max_ctas;                  // at most this many CTAs, striding over the cells (0 = no limit)
   double inv_h[kMaxLevels][3];
   BasisTables B;
 };

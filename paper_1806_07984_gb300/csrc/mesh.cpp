@@ -200,6 +200,45 @@ void Tree::classify(const int8_t* refine_flags) {
   n_conf_skeleton = 0;
   for (const ConfFace& f : conf_all)
     n_conf_skeleton += (skeleton[size_t(f.left)] && skeleton[size_t(f.right)]) ? 1 : 0;
+  // enclave pipeline: chunk of every cell (-1 = skeleton), faces by the later
+  // chunk of their two cells, cells by the latest chunk among their faces
+  const int K = std::max(1, chunks);
+  const int64_t ne = int64_t(encl_cells.size());
+  std::vector<int> chunk_of(n, -1);
+  chunk_off.assign(size_t(K) + 1, 0);
+  for (int k = 0; k <= K; ++k) chunk_off[size_t(k)] = ne * k / K;
+  for (int k = 0; k < K; ++k)
+    for (int64_t p = chunk_off[size_t(k)]; p < chunk_off[size_t(k) + 1]; ++p)
+      chunk_of[size_t(encl_cells[size_t(p)])] = k;
+  std::vector<int> ready(n);
+  for (size_t i = 0; i < n; ++i) ready[i] = chunk_of[i];
+  std::vector<std::vector<ConfFace>> by_chunk(static_cast<size_t>(K));
+  for (size_t i = size_t(n_conf_skeleton); i < conf.size(); ++i) {
+    const ConfFace& f = conf[i];
+    const int r = std::max(chunk_of[size_t(f.left)], chunk_of[size_t(f.right)]);
+    by_chunk[size_t(r)].push_back(f);
+    ready[size_t(f.left)] = std::max(ready[size_t(f.left)], r);
+    ready[size_t(f.right)] = std::max(ready[size_t(f.right)], r);
+  }
+  face_off.assign(size_t(K) + 1, 0);
+  size_t pos = size_t(n_conf_skeleton);
+  for (int k = 0; k < K; ++k) {
+    for (const ConfFace& f : by_chunk[size_t(k)]) conf[pos++] = f;
+    face_off[size_t(k) + 1] = int64_t(pos) - n_conf_skeleton;
+  }
+  corr_off.assign(size_t(K) + 2, 0);
+  for (size_t i = 0; i < n; ++i) ++corr_off[size_t(ready[i] + 1) + 1];
+  for (int g = 0; g <= K; ++g) corr_off[size_t(g) + 1] += corr_off[size_t(g)];
+  corr_cells.assign(n, 0);
+  std::vector<int64_t> fill(corr_off.begin(), corr_off.end() - 1);
+  for (size_t i = 0; i < n; ++i) corr_cells[size_t(fill[size_t(ready[i] + 1)]++)] = int32_t(i);
+}
+
+void Tree::set_chunks(int K) {
+  chunks = std::max(1, K);
+  std::vector<int8_t> flags(cells.size(), 0);
+  for (size_t i = 0; i < cells.size(); ++i) flags[i] = (skeleton[i] && !transition[i]) ? 1 : 0;
+  classify(flags.data());
 }
 
 bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,

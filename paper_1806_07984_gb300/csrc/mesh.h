@@ -72,6 +72,19 @@ class Tree {
   std::vector<ConfFace> conf;
   int64_t n_conf_skeleton = 0;
 
+  // Enclave pipeline of a step (set_chunks(K), recomputed by classify()):
+  // the enclave cells split into K contiguous chunks encl_cells[chunk_off[k] ..
+  // chunk_off[k+1]); the conforming faces after the skeleton ones ordered by the
+  // chunk whose predictor completes their two cells, conf[n_conf_skeleton +
+  // face_off[k] .. n_conf_skeleton + face_off[k+1]); and every cell in
+  // corr_cells, grouped by the stage after which all its face fluxes exist:
+  // group 0 after the skeleton tasks, group k + 1 after chunk k
+  // (corr_cells[corr_off[g] .. corr_off[g+1])).
+  int chunks = 1;
+  std::vector<int64_t> chunk_off, face_off, corr_off;
+  std::vector<int32_t> corr_cells;
+  void set_chunks(int K);
+
   // Rebuild order and faces.  Returns false and sets error() if the mesh is
   // not 2:1 balanced.  Leaves the split as transition cells only.
   bool build();

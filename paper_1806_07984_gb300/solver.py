@@ -16,7 +16,8 @@ class Solver:
     def __init__(self, dim, order, pde="euler", base=(27, 27, 27), max_level=0, cfl=0.1,
                  gamma=1.4, picard_iters=0, precision="fp64", lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), device=None, predictor="picard", limiter=False,
-                 limiter_delta0=1e-4, limiter_eps=1e-3):
+                 limiter_delta0=1e-4, limiter_eps=1e-3, pipeline_chunks=0,
+                 pipeline_ctas=0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda" if device is None else device)
@@ -38,6 +39,8 @@ class Solver:
         cfg.limiter = 1 if limiter else 0
         cfg.limiter_delta0 = limiter_delta0
         cfg.limiter_eps = limiter_eps
+        cfg.pipeline_chunks = pipeline_chunks
+        cfg.pipeline_ctas = pipeline_ctas
         self.cfg = cfg
         self.dim, self.order, self.n, self.nvar = dim, order, order + 1, cfg.nvar
         with torch.cuda.device(self.device):

@@ -112,3 +112,31 @@ def test_limiter_off_by_default_and_guarded():
         s.limiter_flags()
     with pytest.raises(A.AderError):
         Solver(3, 6, "euler", base=(3, 3, 3), cfl=workloads.ADER_CFL[6], limiter=True)
+
+
+def test_pipeline_chunks_do_not_change_the_result():
+    """ader_step with the enclave predictor in K chunks (faces and correctors
+    overlapping later chunks) equals the unchunked step bit for bit, on an AMR
+    mesh with remeshing and with the limiter."""
+    from paper_1806_07984_gb300 import Solver
+    import torch
+    results = []
+    for K, lim, ctas in ((1, False, 0), (3, False, 2), (8, False, 1), (1, True, 0), (5, True, 3)):
+        s = Solver(3, 3, "euler", base=(9, 9, 9), max_level=1, cfl=workloads.ADER_CFL[3],
+                   pipeline_chunks=K, limiter=lim, pipeline_ctas=ctas)
+        s.remesh(s.sphere_flags((0.5, 0.5, 0.5), 0.2))
+        s.classify(s.sphere_flags((0.5, 0.5, 0.5), 0.2))
+        X = s.node_coords()
+        u0 = np.ascontiguousarray(np.moveaxis(
+            workloads.circular_explosion(X, width=0.5 / 9), 0, 1))
+        s.set_state(torch.from_numpy(u0).cuda())
+        s.compute_dt()
+        s.step(2)
+        s.remesh(s.sphere_flags((0.55, 0.5, 0.5), 0.2))
+        s.step(2)
+        results.append((s.get_state().cpu().numpy(), s.dt.item(), s.status()))
+        s.close()
+    for r in results[1:3]:
+        assert np.array_equal(r[0], results[0][0]) and r[1] == results[0][1]
+    assert np.array_equal(results[4][0], results[3][0]) and results[4][1] == results[3][1]
+    assert not np.array_equal(results[3][0], results[0][0])   # the limiter acted
