@@ -44,22 +44,31 @@ __device__ __forceinline__ void rusanov_store(const double (&QL)[PDE::M], const 
   }
 }
 
-template <int DIM, int N, class PDE>
-__device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t f, int lane);
+// Lanes per face: the face nodes rounded up to a power of two (at most 32),
+// so that a warp solves 32 / G faces at once and small faces (2D, low order)
+// keep the FP64 pipe busy with full warps.
+template <int NF>
+struct FaceLanes {
+  static constexpr int G = NF > 16 ? 32 : (NF > 8 ? 16 : (NF > 4 ? 8 : (NF > 2 ? 4 : (NF > 1 ? 2 : 1))));
+  static constexpr int FPW = 32 / G;              // faces per warp
+  static constexpr int PER = (NF + G - 1) / G;    // passes (NF > 32 only)
+};
 
-// One warp per face; a grid smaller than the face count strides over them.
-template <int DIM, int N, class PDE>
-__global__ void riemann_conf_kernel(const RiemannArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t f = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; f < a.nconf; f += warps)
-    riemann_conf_face<DIM, N, PDE>(a, f, lane);
+template <int G>
+__device__ __forceinline__ double group_max(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
+// Conforming face f (valid) on the G lanes of one group; gl = lane in group.
 template <int DIM, int N, class PDE>
-__device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t f, int lane) {
-  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M, PER = (NF + 31) / 32;
-  const ConfFace cf = a.conf[f];
+__device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t f, bool valid, int gl) {
+  constexpr int n = N + 1, NF = ipow(n, DIM - 1), M = PDE::M;
+  using FL_ = FaceLanes<NF>;
+  constexpr int G = FL_::G, PER = FL_::PER;
+  ConfFace cf{};
+  if (valid) cf = a.conf[f];
   const int d = cf.dir;
   const int64_t oL = (int64_t(cf.left) * 2 * DIM + 2 * d + 1) * M * NF;
   const int64_t oR = (int64_t(cf.right) * 2 * DIM + 2 * d + 0) * M * NF;
@@ -68,8 +77,8 @@ __device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t 
   bool ok = true;
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
-    const int fn = lane + 32 * t;
-    if (fn < NF) {
+    const int fn = gl + G * t;
+    if (valid && fn < NF) {
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         QL[t][v] = a.faceQ[oL + v * NF + fn];
@@ -82,12 +91,12 @@ __device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t 
       ok = ok && o1 && o2;
     }
   }
-  smax = warp_max(smax);
-  if (!warp_all(ok) && lane == 0) atomicOr(a.status, kStatusNonPhysical);
+  smax = group_max<G>(smax);
+  if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(a.status, kStatusNonPhysical);
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
-    const int fn = lane + 32 * t;
-    if (fn < NF) {
+    const int fn = gl + G * t;
+    if (valid && fn < NF) {
       double FL[M], FR[M];
 #pragma unroll
       for (int v = 0; v < M; ++v) {
@@ -97,6 +106,20 @@ __device__ __forceinline__ void riemann_conf_face(const RiemannArgs& a, int64_t 
       rusanov_store<DIM, N, PDE>(QL[t], FL, QR[t], FR, smax, a.fstar + oL + fn, a.fstar + oR + fn,
                                  NF);
     }
+  }
+}
+
+// 32 / G faces per warp; a grid smaller than the face count strides over them.
+template <int DIM, int N, class PDE>
+__global__ void riemann_conf_kernel(const RiemannArgs a) {
+  using FL_ = FaceLanes<ipow(N + 1, DIM - 1)>;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / FL_::G, gl = lane % FL_::G;
+  const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w * FL_::FPW < a.nconf;
+       w += warps) {
+    const int64_t f = w * FL_::FPW + sub;
+    riemann_conf_face<DIM, N, PDE>(a, f, f < a.nconf, gl);
   }
 }
 
@@ -437,7 +460,12 @@ cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
   int64_t items = which == 0 ? a.nconf : (which == 1 ? a.nparents * S : a.nparents);
   if (items == 0) return cudaSuccess;
   int64_t blocks = (items * 32 + threads - 1) / threads;
-  if (which == 0 && a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
+  if (which == 0) {
+    constexpr int FPW = FaceLanes<ipow(N + 1, DIM - 1)>::FPW;
+    const int64_t warps = (items + FPW - 1) / FPW;
+    blocks = (warps * 32 + threads - 1) / threads;
+    if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
+  }
   if (which == 0)
     riemann_conf_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
   else if (which == 1)
