@@ -40,8 +40,7 @@ FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 128 FP32 lanes/SM, FMA = 2 
 # case of the same kernel, scaled by cells; per-cell traffic is size
 # independent).  A kernel change invalidates its entry.
 NCU_TRAFFIC_PER_CELL = {
-    "predict_kernel<3,5,Euler,double>": (172.743936e6 + 453.484800e6) / 19683,
-    "predict_kernel<3,5,Euler,float>": (170.238464e6 + 452.787968e6) / 19683,
+    "predict_kernel<3,5,Euler,double>": (171.921408e6 + 453.051648e6) / 19683,
 }
 
 WORKLOADS = {

@@ -532,7 +532,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 // variant's long dependent chains need two CTAs to keep the FP32 pipes busy.
 template <class Real, int NS>
 struct PredictMinBlocks {
-  static constexpr int value = (std::is_same<Real, df64>::value && NS <= 216) ? 2 : 1;
+  static constexpr int value = (!std::is_same<Real, double>::value && NS <= 216) ? 2 : 1;
 };
 
 template <int DIM, int N, class PDE, class Real, int SCHEME = 0>
