@@ -82,6 +82,17 @@ def predictor_bytes_per_cell(dim, order, m):
     return 8 * (2 * m * n ** dim + 2 * 2 * dim * m * n ** (dim - 1))
 
 
+def reduce_over_ranks(torch, seconds, units, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the units all ranks processed (any process-group backend)."""
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -518,12 +529,7 @@ def main():
     elapsed = e0.elapsed_time(e1) / 1e3
     status = s.status()
     if world > 1:
-        tt = torch.tensor([elapsed, float(dofs)], dtype=torch.float64, device=device)
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = tt.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        elapsed, total_dofs = float(mx[0]), float(sm[1])
+        elapsed, total_dofs = reduce_over_ranks(torch, elapsed, dofs, device)
     else:
         total_dofs = float(dofs)
     value = total_dofs / elapsed
@@ -641,9 +647,7 @@ def main():
     torch.cuda.synchronize()
     e2e_time = time.perf_counter() - c0
     if world > 1:
-        tt = torch.tensor([e2e_time], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_time = float(tt[0])
+        e2e_time, _ = reduce_over_ranks(torch, e2e_time, 0, device)
     e2e = {"value": e2e_dofs * world / e2e_time, "unit": "DoF-updates/s",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
            "steps": e2e_steps}
