@@ -55,7 +55,7 @@ def build(verbose=False):
         objs = list(ex.map(_compile, SOURCES))
     if os.path.exists(OUT) and os.path.getmtime(OUT) >= max(os.path.getmtime(o) for o in objs):
         return OUT
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", OUT + ".tmp", *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", OUT + ".tmp", *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

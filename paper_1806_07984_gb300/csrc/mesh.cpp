@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 namespace ader {
 
@@ -108,14 +109,14 @@ void Tree::split(const Key& k) {
 }
 
 void Tree::rebuild_refined() {
-  refined_.clear();
-  for (uint64_t v : leaves_) {
+  refined_.reset(leaves_.size() / 2 + 16);
+  leaves_.for_each([&](uint64_t v, int32_t) {
     Key k = unpack(v);
     while (k.level > 0) {
       k = parent(k);
-      if (!refined_.insert(pack(k)).second) break;
+      if (!refined_.insert(pack(k))) break;
     }
-  }
+  });
 }
 
 void Tree::dfs(const Key& k, std::vector<Key>* out) const {
@@ -144,37 +145,66 @@ void Tree::order_cells(std::vector<Key>* out) const {
 bool Tree::build() {
   order_cells(&cells);
   const int64_t n = int64_t(cells.size());
-  std::unordered_map<uint64_t, int32_t> pos;
-  pos.reserve(size_t(n) * 2);
-  for (int64_t i = 0; i < n; ++i) pos[pack(cells[size_t(i)])] = int32_t(i);
+  KeyMap pos(static_cast<size_t>(n));
+  for (int64_t i = 0; i < n; ++i) pos.insert(pack(cells[size_t(i)]), int32_t(i));
   conf_all.clear();
   parents.clear();
   child_fine.clear();
   transition.assign(size_t(n), 0);
-  std::vector<Key> kids;
-  for (int64_t i = 0; i < n; ++i) {
-    const Key k = cells[size_t(i)];
-    for (int dir = 0; dir < dim_; ++dir) {
-      for (int side = 1; side >= 0; --side) {
-        Key nb = neighbor(k, dir, side);
-        if (side == 1 && is_leaf(nb)) {
-          conf_all.push_back({int32_t(i), pos[pack(nb)], dir, 0});
-        } else if (is_refined(nb)) {
-          touching_children(nb, dir, 1 - side, &kids);
-          parents.push_back({int32_t(i), dir, side, 0});
-          for (const Key& c : kids) {
-            auto it = pos.find(pack(c));
-            if (it == pos.end()) {
-              error_ = "mesh is not 2:1 balanced";
-              return false;
+  // Faces of contiguous cell ranges in parallel (read-only lookups); the
+  // per-range lists are concatenated in range order, so the result equals
+  // the sequential sweep.
+  struct Part {
+    std::vector<ConfFace> conf;
+    std::vector<ParentFace> parents;
+    std::vector<int32_t> child_fine, marked;
+    bool ok = true;
+  };
+  const int nt = int(std::max<int64_t>(1, std::min<int64_t>(
+      int64_t(std::max(1u, std::thread::hardware_concurrency())), std::min<int64_t>(16, n / 4096))));
+  std::vector<Part> parts(static_cast<size_t>(nt));
+  auto sweep = [&](int t) {
+    Part& P = parts[size_t(t)];
+    std::vector<Key> kids;
+    const int64_t b = n * t / nt, e = n * (t + 1) / nt;
+    for (int64_t i = b; i < e && P.ok; ++i) {
+      const Key k = cells[size_t(i)];
+      for (int dir = 0; dir < dim_; ++dir) {
+        for (int side = 1; side >= 0; --side) {
+          Key nb = neighbor(k, dir, side);
+          if (side == 1 && is_leaf(nb)) {
+            P.conf.push_back({int32_t(i), *pos.find(pack(nb)), dir, 0});
+          } else if (is_refined(nb)) {
+            touching_children(nb, dir, 1 - side, &kids);
+            P.parents.push_back({int32_t(i), dir, side, 0});
+            for (const Key& c : kids) {
+              const int32_t* it = pos.find(pack(c));
+              if (!it) {
+                P.ok = false;
+                break;
+              }
+              P.child_fine.push_back(*it);
+              P.marked.push_back(*it);
             }
-            child_fine.push_back(it->second);
-            transition[size_t(it->second)] = 1;
+            P.marked.push_back(int32_t(i));
           }
-          transition[size_t(i)] = 1;
         }
       }
     }
+  };
+  std::vector<std::thread> workers;
+  for (int t = 1; t < nt; ++t) workers.emplace_back(sweep, t);
+  sweep(0);
+  for (std::thread& w : workers) w.join();
+  for (const Part& P : parts) {
+    if (!P.ok) {
+      error_ = "mesh is not 2:1 balanced";
+      return false;
+    }
+    conf_all.insert(conf_all.end(), P.conf.begin(), P.conf.end());
+    parents.insert(parents.end(), P.parents.begin(), P.parents.end());
+    child_fine.insert(child_fine.end(), P.child_fine.begin(), P.child_fine.end());
+    for (int32_t c : P.marked) transition[size_t(c)] = 1;
   }
   classify(nullptr);
   error_.clear();
@@ -244,43 +274,44 @@ void Tree::set_chunks(int K) {
 bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
                   std::vector<int32_t>* coarsen_children) {
   const std::vector<Key> old_cells = cells;
-  std::unordered_map<uint64_t, int32_t> old_index;
-  old_index.reserve(old_cells.size() * 2);
-  for (size_t i = 0; i < old_cells.size(); ++i) old_index[pack(old_cells[i])] = int32_t(i);
-  std::unordered_set<uint64_t> coarsen;
+  KeyMap old_index(old_cells.size());
+  for (size_t i = 0; i < old_cells.size(); ++i) old_index.insert(pack(old_cells[i]), int32_t(i));
+  KeyMap coarsen;
   // 1. refine flagged leaves below max_level
+  std::vector<Key> split_queue;
   for (size_t i = 0; i < old_cells.size(); ++i) {
     const Key& k = old_cells[i];
     if (flags[i] < 0 && k.level > 0) coarsen.insert(pack(k));
-    if (flags[i] > 0 && k.level < max_level_) split(k);
+    if (flags[i] > 0 && k.level < max_level_) {
+      split(k);
+      split_queue.push_back(k);
+    }
+  }
+  // 2. 2:1 face balance to a fixpoint.  Splitting a cell of level L puts
+  // leaves of level L+1 on its faces, which violates the rule only for a
+  // leaf of level <= L-1 across one of them: the leaf covering the
+  // neighbour position.  A worklist over the splits reaches the same (unique,
+  // smallest) balanced refinement as sweeping all leaves until nothing changes.
+  while (!split_queue.empty()) {
+    const Key c = split_queue.back();
+    split_queue.pop_back();
+    for (int dir = 0; dir < dim_; ++dir)
+      for (int side = 0; side < 2; ++side)
+        for (;;) {  // a split cover may leave a child that is still too coarse
+          Key cover = neighbor(c, dir, side);
+          while (cover.level > 0 && !is_leaf(cover)) cover = parent(cover);
+          if (!is_leaf(cover) || cover.level + 2 > c.level + 1) break;
+          split(cover);
+          split_queue.push_back(cover);
+        }
   }
   rebuild_refined();
-  // 2. 2:1 face balance to a fixpoint
-  bool changed = true;
-  std::vector<Key> order;
-  while (changed) {
-    changed = false;
-    order_cells(&order);
-    for (const Key& k : order) {
-      if (!is_leaf(k)) continue;
-      bool need = false;
-      for (int dir = 0; dir < dim_ && !need; ++dir)
-        for (int side = 0; side < 2 && !need; ++side)
-          if (max_level_across(k, dir, side) >= k.level + 2) need = true;
-      if (need) {
-        split(k);
-        changed = true;
-      }
-    }
-    if (changed) rebuild_refined();
-  }
   // 3. coarsen complete families of flagged leaves whose parent stays balanced
   std::vector<uint64_t> fams;
-  for (uint64_t v : coarsen) {
+  coarsen.for_each([&](uint64_t v, int32_t) {
     Key k = unpack(v);
-    if (!is_leaf(k)) continue;
-    fams.push_back(pack(parent(k)));
-  }
+    if (is_leaf(k)) fams.push_back(pack(parent(k)));
+  });
   std::sort(fams.begin(), fams.end());
   fams.erase(std::unique(fams.begin(), fams.end()), fams.end());
   std::vector<Key> approved;
@@ -316,14 +347,14 @@ bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
   coarsen_children->clear();
   for (const Key& k : cells) {
     TransferItem t{0, 0, 0, 0};
-    auto it = old_index.find(pack(k));
-    if (it != old_index.end()) {
+    const int32_t* it = old_index.find(pack(k));
+    if (it) {
       t.kind = 0;
-      t.src = it->second;
+      t.src = *it;
     } else if (k.level > 0 && old_index.count(pack(parent(k)))) {
       Key p = parent(k);
       t.kind = 1;
-      t.src = old_index[pack(p)];
+      t.src = *old_index.find(pack(p));
       int s[3] = {0, 0, 0};
       for (int d = 0; d < dim_; ++d) s[d] = k.x[d] - 3 * p.x[d];
       t.child = s[0] + 3 * s[1] + 9 * s[2];
@@ -334,12 +365,12 @@ bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
         for (int sy = 0; sy < 3; ++sy)
           for (int sx = 0; sx < 3; ++sx) {
             int s[3] = {sx, sy, sz};
-            auto c = old_index.find(pack(child(k, s)));
-            if (c == old_index.end()) {
+            const int32_t* c = old_index.find(pack(child(k, s)));
+            if (!c) {
               error_ = "remesh changed a cell by more than one level";
               return false;
             }
-            coarsen_children->push_back(c->second);
+            coarsen_children->push_back(*c);
           }
     }
     plan->push_back(t);

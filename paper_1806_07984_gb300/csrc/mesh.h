@@ -9,8 +9,6 @@
 #pragma once
 #include <cstdint>
 #include <string>
-#include <unordered_map>
-#include <unordered_set>
 #include <vector>
 
 namespace ader {
@@ -22,6 +20,87 @@ struct Key {
 
 uint64_t pack(const Key& k);
 Key unpack(uint64_t v);
+
+// Open-addressing hash table from packed cell keys to int32 values (linear
+// probing, power-of-two capacity, splitmix64 mixing of the key, tombstones on
+// erase).  The tree's hot operations are lookups of packed keys; this keeps
+// them to one or two cache lines each.  The two all-ones patterns mark empty
+// and erased slots (a packed key's top nibble holds a level <= 7).
+class KeyMap {
+ public:
+  explicit KeyMap(size_t expect = 16) { reset(expect); }
+  void reset(size_t expect) {
+    size_t cap = 16;
+    while (cap < 2 * expect) cap <<= 1;
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, 0);
+    size_ = used_ = 0;
+  }
+  size_t size() const { return size_; }
+  // returns true when k was not present
+  bool insert(uint64_t k, int32_t v = 0) {
+    if (2 * (used_ + 1) > keys_.size()) grow();
+    size_t i = slot(k), tomb = SIZE_MAX;
+    for (;; i = (i + 1) & (keys_.size() - 1)) {
+      if (keys_[i] == k) return false;
+      if (keys_[i] == kErased && tomb == SIZE_MAX) tomb = i;
+      if (keys_[i] == kEmpty) break;
+    }
+    if (tomb != SIZE_MAX) {
+      i = tomb;
+    } else {
+      ++used_;
+    }
+    keys_[i] = k;
+    vals_[i] = v;
+    ++size_;
+    return true;
+  }
+  const int32_t* find(uint64_t k) const {
+    for (size_t i = slot(k);; i = (i + 1) & (keys_.size() - 1)) {
+      if (keys_[i] == k) return &vals_[i];
+      if (keys_[i] == kEmpty) return nullptr;
+    }
+  }
+  bool count(uint64_t k) const { return find(k) != nullptr; }
+  void erase(uint64_t k) {
+    for (size_t i = slot(k);; i = (i + 1) & (keys_.size() - 1)) {
+      if (keys_[i] == k) {
+        keys_[i] = kErased;
+        --size_;
+        return;
+      }
+      if (keys_[i] == kEmpty) return;
+    }
+  }
+  template <class F>
+  void for_each(F&& f) const {
+    for (size_t i = 0; i < keys_.size(); ++i)
+      if (keys_[i] != kEmpty && keys_[i] != kErased) f(keys_[i], vals_[i]);
+  }
+
+ private:
+  static constexpr uint64_t kEmpty = ~uint64_t(0);
+  static constexpr uint64_t kErased = ~uint64_t(0) - 1;
+  size_t slot(uint64_t k) const {
+    k += 0x9e3779b97f4a7c15ull;  // splitmix64 finaliser
+    k = (k ^ (k >> 30)) * 0xbf58476d1ce4e5b9ull;
+    k = (k ^ (k >> 27)) * 0x94d049bb133111ebull;
+    return size_t(k ^ (k >> 31)) & (keys_.size() - 1);
+  }
+  void grow() {
+    std::vector<uint64_t> ok;
+    std::vector<int32_t> ov;
+    ok.swap(keys_);
+    ov.swap(vals_);
+    reset(size_ > 8 ? 2 * size_ : 16);
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ok[i] != kEmpty && ok[i] != kErased) insert(ok[i], ov[i]);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<int32_t> vals_;
+  size_t size_ = 0, used_ = 0;
+};
 
 // One transition: the coarse cell's face (dir, coarse_side) is split into
 // 3^(d-1) child faces; child sigma (lowest tangential direction fastest)
@@ -123,8 +202,8 @@ class Tree {
   int dim_ = 0;
   int base_[3] = {1, 1, 1};
   int max_level_ = 0;
-  std::unordered_set<uint64_t> leaves_;
-  std::unordered_set<uint64_t> refined_;
+  KeyMap leaves_;
+  KeyMap refined_;
   std::string error_;
 };
 
