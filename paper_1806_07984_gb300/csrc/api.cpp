@@ -51,6 +51,9 @@ struct ader_ctx {
   unsigned long long* rate_cand = nullptr;
   uint32_t* status_cand = nullptr;
   int num_sms = 0;
+  TransferItem* plan_dev = nullptr;  // remesh transfer plan and child lists
+  int32_t* kids_dev = nullptr;
+  int64_t plan_cap = 0, kids_cap = 0;
   std::string err;
   int64_t launches = 0;
 };
@@ -539,7 +542,8 @@ void ader_destroy(ader_ctx* c) {
                   (void*)c->status, (void*)c->dt_scratch, (void*)c->u_old, (void*)c->bounds,
                   (void*)c->lim_flags, (void*)c->lim_list, (void*)c->fix_list, (void*)c->nbr,
                   (void*)c->force, (void*)c->lim_counts, (void*)c->rate_cand,
-                  (void*)c->status_cand, (void*)c->corr_cells})
+                  (void*)c->status_cand, (void*)c->corr_cells, (void*)c->plan_dev,
+                  (void*)c->kids_dev})
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev_chunk)
     if (e) cudaEventDestroy(e);
@@ -752,20 +756,23 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   }
   const int64_t C_new = int64_t(c->tree.cells.size());
   c->force_set = false;
-  // keep the old state while the cell-sized buffers grow
+  // Keep the old state while the mesh lists are uploaded: in u* (free between
+  // steps) when the cell buffers keep their capacity, else in a new buffer.
   const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
-  double* old_u = nullptr;
-  CK(cudaMalloc(&old_u, cell_bytes * size_t(std::max<int64_t>(C_old, 1))), "cudaMalloc remesh");
+  const bool in_place = C_new <= c->cap;
+  double* old_u = in_place ? c->ustar : nullptr;
+  if (!in_place)
+    CK(cudaMalloc(&old_u, cell_bytes * size_t(std::max<int64_t>(C_old, 1))), "cudaMalloc remesh");
   CK(cudaMemcpy(old_u, c->u, cell_bytes * size_t(C_old), cudaMemcpyDeviceToDevice), "copy u");
   ader_status st = upload_mesh(c);
   if (st != ADER_OK) {
-    cudaFree(old_u);
+    if (!in_place) cudaFree(old_u);
     return st;
   }
-  TransferItem* d_plan = nullptr;
-  int32_t* d_kids = nullptr;
-  CK(cudaMalloc(&d_plan, sizeof(TransferItem) * plan.size()), "cudaMalloc plan");
-  CK(cudaMalloc(&d_kids, sizeof(int32_t) * std::max<size_t>(kids.size(), 1)), "cudaMalloc kids");
+  CK(grow(&c->plan_dev, &c->plan_cap, int64_t(plan.size())), "cudaMalloc plan");
+  CK(grow(&c->kids_dev, &c->kids_cap, std::max<int64_t>(int64_t(kids.size()), 1)), "cudaMalloc kids");
+  TransferItem* d_plan = c->plan_dev;
+  int32_t* d_kids = c->kids_dev;
   CK(cudaMemcpy(d_plan, plan.data(), sizeof(TransferItem) * plan.size(), cudaMemcpyHostToDevice),
      "upload plan");
   if (!kids.empty())
@@ -782,9 +789,7 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   a.B = c->B;
   cudaError_t e = do_transfer(c, a, nullptr);
   cudaError_t e2 = cudaDeviceSynchronize();
-  cudaFree(old_u);
-  cudaFree(d_plan);
-  cudaFree(d_kids);
+  if (!in_place) cudaFree(old_u);
   if (e != cudaSuccess) return cuda_fail(c, e, "transfer");
   if (e2 != cudaSuccess) return cuda_fail(c, e2, "transfer sync");
   return ADER_OK;
