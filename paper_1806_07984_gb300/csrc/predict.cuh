@@ -146,13 +146,24 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   constexpr bool kDinRegs = std::is_same<Real, float>::value;
   constexpr bool kRollSlices = std::is_same<Real, df64>::value;
   constexpr int kDr = kDinRegs ? n : 1;
+  // FP32, 3D, n = 6, 7: the y and z line contractions of a thread in plane z
+  // start at element z (cyclically).  Warps that straddle two z-planes then
+  // read different rows/planes in the two parts at each step, which removes
+  // most shared-memory bank conflicts of those contractions (n^2 = 36, 49 do
+  // not divide into 32-lane warps).
+  constexpr bool kRot = kDinRegs && DIM == 3 && (n == 6 || n == 7);
+  const int rz = kRot ? id[2] : 0;
   __syncthreads();
   Real Dr[DIM][kDr];
   if constexpr (kDinRegs) {
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int j = 0; j < kDr; ++j) Dr[d][j] = sDh[cl][d][id[d] * n + j];
+      for (int j = 0; j < kDr; ++j) {
+        int jj = j;
+        if (kRot && d > 0) jj = (j + rz) % n;
+        Dr[d][j] = sDh[cl][d][id[d] * n + jj];
+      }
   }
 
   // ---- tensor-core set-up: operand tiles, B = D/h_d splits, TMEM, mbarrier
@@ -326,7 +337,12 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
               dj = Dr[d][j < kDr ? j : 0];
             else
               dj = sDh[cl][d][id[d] * n + j];
-            g[v] = fma(dj, line[j * stride[d]], g[v]);
+            int jj = j;
+            if (kRot && d > 0) {
+              jj = j + rz;
+              jj = jj >= n ? jj - n : jj;
+            }
+            g[v] = fma(dj, line[jj * stride[d]], g[v]);
           }
         }
       }
