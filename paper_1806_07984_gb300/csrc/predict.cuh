@@ -39,6 +39,14 @@ struct PredictShape {
   static constexpr int THREADS = CPB * NS;
 };
 
+// Contraction steps: a plain FMA in FP32/FP64; for double-float the
+// compensated accumulation (no renormalisation per term) followed by one
+// `settle` at the end of the sum.
+__device__ __forceinline__ float fma_acc(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_acc(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float settle(float a) { return a; }
+__device__ __forceinline__ double settle(double a) { return a; }
+
 // Dynamic shared memory: fluxes of one slice fb[CPB][DIM][M][NS] (Real),
 // Q-bar qs[CPB][M][NS] (Real), and for the FP32 variant an FP64 reduction
 // buffer red[CPB][M][NS].
@@ -320,9 +328,11 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
         for (int v = 0; v < M; ++v) {
           const Real* line = line0 + v * NS;
 #pragma unroll
-          for (int j = 0; j < n; ++j) g[v] = fma(drow[j], line[j * sd], g[v]);
+          for (int j = 0; j < n; ++j) g[v] = fma_acc(drow[j], line[j * sd], g[v]);
         }
       }
+#pragma unroll
+      for (int v = 0; v < M; ++v) g[v] = settle(g[v]);
     } else {
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
@@ -400,7 +410,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
         for (int k = 0; k < n; ++k) {
           const Real c = sMd[k * n + l];
 #pragma unroll
-          for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
+          for (int v = 0; v < M; ++v) acc[k][v] = fma_acc(c, g[v], acc[k][v]);
         }
       };
       if constexpr (kRollSlices) {
@@ -415,7 +425,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
       for (int k = 0; k < n; ++k)
 #pragma unroll
-        for (int v = 0; v < M; ++v) q[k][v] = acc[k][v];
+        for (int v = 0; v < M; ++v) q[k][v] = settle(acc[k][v]);
     }
     // Time averages of the final iterate and of its fluxes.
 #pragma unroll
@@ -429,11 +439,11 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       PDE::fluxes(q[k], f, gamma);
       const Real wk = sw[k];
 #pragma unroll
-      for (int v = 0; v < M; ++v) qb[v] = fma(wk, q[k][v], qb[v]);
+      for (int v = 0; v < M; ++v) qb[v] = fma_acc(wk, q[k][v], qb[v]);
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
 #pragma unroll
-        for (int v = 0; v < M; ++v) Fb[d][v] = fma(wk, f[d][v], Fb[d][v]);
+        for (int v = 0; v < M; ++v) Fb[d][v] = fma_acc(wk, f[d][v], Fb[d][v]);
     };
     if constexpr (kRollSlices) {
 #pragma unroll 1
@@ -441,6 +451,12 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     } else {
 #pragma unroll
       for (int k = 0; k < n; ++k) average(k);
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      qb[v] = settle(qb[v]);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) Fb[d][v] = settle(Fb[d][v]);
     }
   }
   bool finite = true;
