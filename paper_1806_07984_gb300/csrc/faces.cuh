@@ -123,6 +123,65 @@ __global__ void riemann_conf_kernel(const RiemannArgs a) {
   }
 }
 
+// Faces whose node count is above 32 and not a multiple of 32 (3D, N = 5, 6):
+// 8 faces per CTA, one thread per face node, the speed of each face reduced
+// with shared-memory atomics on the FP64 bit pattern (non-negative values);
+// no lane idles across the two passes a warp per face would take.
+template <int NF>
+struct FaceBlock {
+  static constexpr bool kUse = NF > 32 && NF % 32 != 0;
+  static constexpr int FPC = 8;
+  static constexpr int THREADS = (FPC * NF + 31) / 32 * 32;
+};
+
+template <int DIM, int N, class PDE>
+__global__ void __launch_bounds__(FaceBlock<ipow(N + 1, DIM - 1)>::THREADS)
+    riemann_conf_block_kernel(const RiemannArgs a) {
+  constexpr int NF = ipow(N + 1, DIM - 1), M = PDE::M;
+  using FB = FaceBlock<NF>;
+  __shared__ unsigned long long smax[FB::FPC];
+  __shared__ int bad;
+  const int slot = threadIdx.x / NF, fn = threadIdx.x % NF;
+  const int64_t groups = (a.nconf + FB::FPC - 1) / FB::FPC;
+  for (int64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
+    if (threadIdx.x < FB::FPC) smax[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    const int64_t f = gidx * FB::FPC + slot;
+    const bool valid = slot < FB::FPC && f < a.nconf;
+    ConfFace cf{};
+    if (valid) cf = a.conf[f];
+    const int d = cf.dir;
+    const int64_t oL = (int64_t(cf.left) * 2 * DIM + 2 * d + 1) * M * NF;
+    const int64_t oR = (int64_t(cf.right) * 2 * DIM + 2 * d + 0) * M * NF;
+    double QL[M], QR[M];
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        QL[v] = a.faceQ[oL + v * NF + fn];
+        QR[v] = a.faceQ[oR + v * NF + fn];
+      }
+      bool o1, o2;
+      const double l = fmax(PDE::max_speed(QL, d, a.gamma, &o1), PDE::max_speed(QR, d, a.gamma, &o2));
+      atomicMax(&smax[slot], static_cast<unsigned long long>(__double_as_longlong(l)));
+      if (!(o1 && o2)) bad = 1;
+    }
+    __syncthreads();
+    if (valid) {
+      const double sp = __longlong_as_double(static_cast<long long>(smax[slot]));
+      double FL[M], FR[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        FL[v] = a.faceF[oL + v * NF + fn];
+        FR[v] = a.faceF[oR + v * NF + fn];
+      }
+      rusanov_store<DIM, N, PDE>(QL, FL, QR, FR, sp, a.fstar + oL + fn, a.fstar + oR + fn, NF);
+    }
+    if (threadIdx.x == 0 && bad) atomicOr(a.status, kStatusNonPhysical);
+    __syncthreads();
+  }
+}
+
 // Tangential interpolation of one coarse face block onto child sub-face
 // (s0, s1) at face node (ia, ib): X_v = sum_j P[s1][ib][j] sum_i P[s0][ia][i] X(i + n j).
 template <int DIM, int N, int M>
@@ -466,7 +525,12 @@ cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
     blocks = (warps * 32 + threads - 1) / threads;
     if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
   }
-  if (which == 0)
+  if (which == 0 && FaceBlock<ipow(N + 1, DIM - 1)>::kUse) {
+    using FB = FaceBlock<ipow(N + 1, DIM - 1)>;
+    int64_t b = (items + FB::FPC - 1) / FB::FPC;
+    if (a.max_ctas > 0 && b > a.max_ctas) b = a.max_ctas;
+    riemann_conf_block_kernel<DIM, N, PDE><<<unsigned(b), FB::THREADS, 0, s>>>(a);
+  } else if (which == 0)
     riemann_conf_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
   else if (which == 1)
     riemann_child_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
