@@ -666,7 +666,7 @@ def main():
                        "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
                        "remesh_every": wl["remesh_every"],
                        "pipeline_chunks": args.pipeline or 8,
-                       "pipeline_ctas_per_sm": args.pipeline_ctas or 1},
+                       "pipeline_ctas_per_sm": args.pipeline_ctas or 2},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
             "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -120,7 +120,7 @@ typedef struct {
   double limiter_delta0;     /* relaxed maximum principle: delta = max(delta0, eps (max - min)); */
   double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
   int pipeline_chunks;       /* ader_step: enclave chunks K (0 selects 8, 1 disables); see ader_step */
-  int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 1) */
+  int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 2) */
 } ader_config;
 
 typedef struct ader_ctx ader_ctx;

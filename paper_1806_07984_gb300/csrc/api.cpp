@@ -673,7 +673,7 @@ ader_status step_pipelined(ader_ctx* c, double* dt_dev) {
   CK(do_predict(c, ps, c->s_hi), "skeleton predictor");
   ader_status st = enqueue_riemann(c, ADER_SKELETON, c->s_hi);
   if (st != ADER_OK) return st;
-  const int cap = c->num_sms * (c->cfg.pipeline_ctas > 0 ? c->cfg.pipeline_ctas : 1);
+  const int cap = c->num_sms * (c->cfg.pipeline_ctas > 0 ? c->cfg.pipeline_ctas : 2);
   auto correct_group = [&](int g) -> ader_status {
     const int64_t b = t.corr_off[size_t(g)], e = t.corr_off[size_t(g) + 1];
     if (e > b) {
