@@ -394,9 +394,11 @@ def time_predictor(s, torch, reps=3):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def cpu_baseline(wl_name, wl, seconds=15.0):
-    """Oracle (numpy FP64, one BLAS thread) on a bounded sample: full oracle
-    steps on the same PDE/order/refinement rule on a base 3^3 mesh."""
+def cpu_baseline(wl_name, wl, seconds=15.0, cores=1):
+    """Oracle (numpy FP64, one BLAS thread per process) on a bounded sample:
+    full oracle steps on the same PDE/order/refinement rule on a base 3^3
+    mesh; with cores > 1 that many independent processes run at once and
+    their throughputs add up."""
     code = r"""
 import os, sys, time, json
 import numpy as np
@@ -427,15 +429,21 @@ dofs = len(m.cells) * (dim + 2) * (order + 1) ** dim
 print(json.dumps(dict(value=dofs * steps / el, cells=len(m.cells), steps=steps, seconds=el)))
 """ % (ROOT, wl["dim"], wl["order"], wl["max_level"], wl["radius"], seconds)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=600)
-    if r.returncode != 0:
-        return {"error": r.stderr[-400:]}
-    res = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": res["value"], "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{res['steps']} oracle steps of the same PDE/order/AMR rule on a base-3^"
-                      f"{wl['dim']} mesh with {res['cells']} cells ({res['seconds']:.1f} s, "
-                      "numpy FP64, 1 BLAS thread)"}
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(cores)]
+    results = []
+    for pr in procs:
+        out, err = pr.communicate(timeout=600)
+        if pr.returncode != 0:
+            return {"error": err[-400:]}
+        results.append(json.loads(out.strip().splitlines()[-1]))
+    res = results[0]
+    what = (f"{res['steps']} oracle steps of the same PDE/order/AMR rule on a base-3^{wl['dim']} mesh "
+            f"with {res['cells']} cells ({res['seconds']:.1f} s, numpy FP64, 1 BLAS thread)")
+    if cores > 1:
+        what = f"{cores} concurrent processes, each " + what
+    return {"value": sum(r["value"] for r in results), "unit": "DoF-updates/s", "cores": cores,
+            "kind": "oracle", "sample": what}
 
 
 def reference_arm(args, wl_name, wl):
@@ -671,6 +679,8 @@ def main():
             "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
+        line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, seconds=10.0,
+                                                      cores=os.cpu_count() or 1)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
