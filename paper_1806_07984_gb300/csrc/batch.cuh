@@ -11,6 +11,7 @@
 // A whole multi-step run is one CUDA graph of these phase kernels; phase
 // boundaries are kernel boundaries, so no CTA ever waits on another.
 #pragma once
+#include <type_traits>
 #include "batch_types.h"
 #include "faces.cuh"
 #include "predict.cuh"
@@ -45,8 +46,11 @@ __device__ __forceinline__ void batch_predict_item(const BatchArgs& a, const Bat
   }
 }
 
+// FP32: registers capped for two resident CTAs per SM (the predictor is
+// shared-memory bound and needs the warps); FP64 keeps one (FP64-pipe bound).
 template <int DIM, class PDE, class Real>
-__global__ void __launch_bounds__(256) batch_predict_kernel(const BatchArgs a, int slot) {
+__global__ void __launch_bounds__(256, std::is_same<Real, float>::value ? 2 : 1)
+    batch_predict_kernel(const BatchArgs a, int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (;;) {
     const int it = take_item(a.counters + slot);
