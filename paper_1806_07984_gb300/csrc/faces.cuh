@@ -16,7 +16,9 @@
 //                   atomicMax per CTA.
 // * transfer      - remesh volume transfer: copy, interpolate into a child,
 //                   or L2-project 3^d children onto the parent.
-// All in FP64.  Face kernels map one warp to one face (lanes over face nodes).
+// All in FP64.  Conforming faces: 32/G faces per warp for faces of at most 32
+// nodes (G lanes each), 8 faces per CTA for 36 or 49 nodes; child faces: one
+// warp per face (lanes over face nodes).
 #pragma once
 #include "kernels.h"
 #include "pde.cuh"
