@@ -121,6 +121,8 @@ typedef struct {
   double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
   int pipeline_chunks;       /* ader_step: enclave chunks K (0 selects 8, 1 disables); see ader_step */
   int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 2) */
+  int eager_steps;           /* 1: ader_step launches every kernel itself instead of replaying a
+                                CUDA graph of one step (captured once per mesh and dt pointer) */
 } ader_config;
 
 typedef struct ader_ctx ader_ctx;
@@ -214,7 +216,11 @@ ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_de
  * corrector work (FP64) overlaps the remaining predictor chunks.  Those face
  * and corrector kernels are capped at cfg.pipeline_ctas CTAs per SM (striding
  * over their items) so that they share the SMs with predictor CTAs instead of
- * taking them over.  The result does not depend on K or the cap. */
+ * taking them over.  The result does not depend on K or the cap.
+ * Unless cfg.eager_steps is set, the first call captures one step (both
+ * streams, all launches) into a CUDA graph and every step replays it; a
+ * remesh, a reclassification, a change of forced limiter cells or another
+ * dt pointer recaptures.  If the capture fails the steps run eagerly. */
 ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
 
 /* Dynamic adaptivity (Sec. 2.3): flags per cell in mesh order (+1 refine,

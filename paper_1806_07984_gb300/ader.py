@@ -62,7 +62,7 @@ class ader_config(ctypes.Structure):
                 ("picard_iters", ctypes.c_int), ("prec", ctypes.c_int), ("predictor", ctypes.c_int),
                 ("limiter", ctypes.c_int), ("limiter_delta0", ctypes.c_double),
                 ("limiter_eps", ctypes.c_double), ("pipeline_chunks", ctypes.c_int),
-                ("pipeline_ctas", ctypes.c_int)]
+                ("pipeline_ctas", ctypes.c_int), ("eager_steps", ctypes.c_int)]
 
 
 _lib = None

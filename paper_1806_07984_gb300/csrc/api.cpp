@@ -51,6 +51,11 @@ struct ader_ctx {
   unsigned long long* rate_cand = nullptr;
   uint32_t* status_cand = nullptr;
   int num_sms = 0;
+  cudaGraphExec_t step_exec = nullptr;  // one captured step for the current mesh
+  const double* graph_dt = nullptr;
+  int64_t step_graph_launches = 0;
+  bool graphs_ok = true;
+  bool warm = false;  // an eager step ran since the mesh lists last changed
   TransferItem* plan_dev = nullptr;  // remesh transfer plan and child lists
   int32_t* kids_dev = nullptr;
   int64_t plan_cap = 0, kids_cap = 0;
@@ -185,8 +190,16 @@ ader_status ensure_cells(ader_ctx* c, int64_t need) {
   return ADER_OK;
 }
 
+// The captured step bakes in the mesh lists, their sizes and pointers.
+void drop_step_graph(ader_ctx* c) {
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  c->step_exec = nullptr;
+  c->warm = false;
+}
+
 // Upload levels, cell lists and face lists of the current tree (synchronous).
 ader_status upload_mesh(ader_ctx* c) {
+  drop_step_graph(c);
   const Tree& t = c->tree;
   const int64_t C = int64_t(t.cells.size());
   ader_status st = ensure_cells(c, C);
@@ -536,6 +549,7 @@ void ader_destroy(ader_ctx* c) {
   if (!c) return;
   if (c->s_hi) cudaStreamSynchronize(c->s_hi);
   if (c->s_lo) cudaStreamSynchronize(c->s_lo);
+  drop_step_graph(c);
   for (void* p : {(void*)c->u, (void*)c->ustar, (void*)c->faceQ, (void*)c->faceF, (void*)c->fstar,
                   (void*)c->level, (void*)c->all_cells, (void*)c->skel_cells, (void*)c->encl_cells,
                   (void*)c->conf, (void*)c->parents, (void*)c->child_fine, (void*)c->rate,
@@ -706,11 +720,66 @@ ader_status step_pipelined(ader_ctx* c, double* dt_dev) {
   return enqueue_finish(c, dt_dev, dt_dev, c->s_hi);
 }
 
+// One step's work on s_hi / s_lo (joined back into s_hi at the end).
+ader_status enqueue_step(ader_ctx* c, double* dt_dev) {
+  if (c->tree.chunks > 1) return step_pipelined(c, dt_dev);
+  CK(cudaEventRecord(c->ev_step, c->s_hi), "event");
+  CK(cudaStreamWaitEvent(c->s_lo, c->ev_step, 0), "event");
+  PredictArgs ps = predict_args(c, dt_dev, ADER_SKELETON);
+  CK(do_predict(c, ps, c->s_hi), "skeleton predictor");
+  ader_status st = enqueue_riemann(c, ADER_SKELETON, c->s_hi);
+  if (st != ADER_OK) return st;
+  PredictArgs pe = predict_args(c, dt_dev, ADER_ENCLAVE);
+  CK(do_predict(c, pe, c->s_lo), "enclave predictor");
+  CK(cudaEventRecord(c->ev_lo, c->s_lo), "event");
+  CK(cudaStreamWaitEvent(c->s_hi, c->ev_lo, 0), "event");
+  st = enqueue_riemann(c, ADER_ENCLAVE, c->s_hi);
+  if (st != ADER_OK) return st;
+  return enqueue_correct(c, dt_dev, dt_dev, c->s_hi);
+}
+
+// Capture one step (both streams) into a CUDA graph for this mesh and dt
+// pointer.  On any capture failure the context keeps launching eagerly.
+void capture_step(ader_ctx* c, double* dt_dev) {
+  drop_step_graph(c);
+  const int64_t before = c->launches;
+  if (cudaStreamBeginCapture(c->s_hi, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    c->graphs_ok = false;
+    return;
+  }
+  const ader_status st = enqueue_step(c, dt_dev);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->s_hi, &g);
+  c->step_graph_launches = c->launches - before;
+  c->launches = before;
+  cudaGetLastError();
+  if (st != ADER_OK || e != cudaSuccess || !g ||
+      cudaGraphInstantiate(&c->step_exec, g, 0) != cudaSuccess) {
+    c->step_exec = nullptr;
+    c->graphs_ok = false;
+    cudaGetLastError();
+  } else {
+    c->graph_dt = dt_dev;
+  }
+  if (g) cudaGraphDestroy(g);
+}
+
 ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
   if (!c || !dt_dev || nsteps < 0) return ADER_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaEventRecord(c->ev_begin, s), "event");
   CK(cudaStreamWaitEvent(c->s_hi, c->ev_begin, 0), "event");
+  // capture once this mesh has run one eager step (every kernel configured)
+  if (nsteps > 0 && c->graphs_ok && !c->cfg.eager_steps && c->warm) {
+    if (!c->step_exec || c->graph_dt != dt_dev) capture_step(c, dt_dev);
+    if (c->step_exec) {
+      for (int k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(c->step_exec, c->s_hi), "step graph launch");
+        c->launches += c->step_graph_launches;
+      }
+      nsteps = 0;
+    }
+  }
   for (int k = 0; k < nsteps; ++k) {
     if (c->tree.chunks > 1) {
       ader_status st = step_pipelined(c, dt_dev);
@@ -732,6 +801,7 @@ ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
     st = enqueue_correct(c, dt_dev, dt_dev, c->s_hi);
     if (st != ADER_OK) return st;
   }
+  if (nsteps > 0) c->warm = true;
   CK(cudaEventRecord(c->ev_end, c->s_hi), "event");
   CK(cudaStreamWaitEvent(s, c->ev_end, 0), "event");
   return ADER_OK;
@@ -923,6 +993,7 @@ ader_status ader_limiter_flags(ader_ctx* c, uint32_t* flags, int on_device, int6
 ader_status ader_limiter_force(ader_ctx* c, const uint8_t* force) {
   if (!c || !c->cfg.limiter) return ADER_ERR_ARG;
   CK(cudaDeviceSynchronize(), "sync before limiter force");
+  drop_step_graph(c);
   if (!force) {
     c->force_set = false;
     return ADER_OK;

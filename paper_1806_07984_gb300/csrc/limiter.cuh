@@ -541,20 +541,27 @@ cudaError_t launch_limiter_t(LimiterKernel which, const LimiterArgs& a, int grid
     if (a.ncells == 0) return cudaSuccess;
     const size_t bytes = sizeof(double) * size_t(S * n + 16 * M + M * L::NS +
                                                  M * partial_scratch<DIM, N>());
-    if (which == LimiterKernel::kBounds) {
-      auto k = limiter_bounds_kernel<DIM, N, PDE>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      k<<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
-    } else {
-      auto k = limiter_detect_kernel<DIM, N, PDE>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      k<<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
+    static bool configured = false;  // per process: set once, outside any graph capture
+    if (!configured) {
+      cudaFuncSetAttribute(limiter_bounds_kernel<DIM, N, PDE>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+      cudaFuncSetAttribute(limiter_detect_kernel<DIM, N, PDE>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+      configured = true;
     }
+    if (which == LimiterKernel::kBounds)
+      limiter_bounds_kernel<DIM, N, PDE><<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
+    else
+      limiter_detect_kernel<DIM, N, PDE><<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
   } else if (which == LimiterKernel::kFV) {
     const size_t bytes = sizeof(double) * size_t(FvSmem<DIM, N, M>::doubles);
-    auto k = limiter_fv_kernel<DIM, N, PDE>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    k<<<unsigned(grid), L::THREADS, bytes, s>>>(a);
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(limiter_fv_kernel<DIM, N, PDE>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+      configured = true;
+    }
+    limiter_fv_kernel<DIM, N, PDE><<<unsigned(grid), L::THREADS, bytes, s>>>(a);
   } else {
     limiter_fix_kernel<DIM, N, PDE><<<unsigned(grid), 128, 0, s>>>(a);
   }

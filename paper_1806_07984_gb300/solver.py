@@ -17,7 +17,7 @@ class Solver:
                  gamma=1.4, picard_iters=0, precision="fp64", lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), device=None, predictor="picard", limiter=False,
                  limiter_delta0=1e-4, limiter_eps=1e-3, pipeline_chunks=0,
-                 pipeline_ctas=0):
+                 pipeline_ctas=0, eager_steps=False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda" if device is None else device)
@@ -41,6 +41,7 @@ class Solver:
         cfg.limiter_eps = limiter_eps
         cfg.pipeline_chunks = pipeline_chunks
         cfg.pipeline_ctas = pipeline_ctas
+        cfg.eager_steps = 1 if eager_steps else 0
         self.cfg = cfg
         self.dim, self.order, self.n, self.nvar = dim, order, order + 1, cfg.nvar
         with torch.cuda.device(self.device):
