@@ -42,7 +42,7 @@ struct ader_ctx {
   // lists, neighbour table, forced cells; the candidate stage reports into
   // rate_cand / status_cand
   SubcellTables T{};
-  double *u_old = nullptr, *bounds = nullptr;
+  double *u_old = nullptr, *bounds = nullptr, *fv_scratch = nullptr;
   uint32_t* lim_flags = nullptr;
   int32_t *lim_list = nullptr, *fix_list = nullptr, *nbr = nullptr;
   uint8_t* force = nullptr;
@@ -358,6 +358,7 @@ LimiterArgs limiter_args(ader_ctx* c, const double* dt) {
   a.eps = c->cfg.limiter_eps > 0.0 ? c->cfg.limiter_eps : 1e-3;
   a.rate_max = c->rate;
   a.status = c->status;
+  a.fv_scratch = c->fv_scratch;
   std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
   a.B = c->B;
   a.T = c->T;
@@ -449,8 +450,7 @@ bool valid_config(const ader_config* cfg, std::string* why) {
     return *why = "pipeline_chunks must be in 0..64", false;
   if (cfg->pipeline_ctas < 0 || cfg->pipeline_ctas > 32)
     return *why = "pipeline_ctas must be in 0..32", false;
-  if (cfg->limiter && cfg->dim == 3 && cfg->order > 5)
-    return *why = "subcell limiter: 3D orders 1..5", false;
+
   return true;
 }
 
@@ -527,6 +527,9 @@ ader_status ader_init(const ader_config* cfg, ader_ctx** out) {
     return fail(ADER_ERR_CUDA);
   if (cfg->limiter) {
     make_subcells(c->n, &c->T);
+    const int64_t slot = cfg->dim == 3 ? limiter_fv_scratch_3d(cfg->order, cfg->pde == ADER_EULER ? 0 : 1) : 0;
+    if (slot > 0 && cudaMalloc(&c->fv_scratch, sizeof(double) * size_t(slot) * 2 * c->num_sms) != cudaSuccess)
+      return fail(ADER_ERR_OOM);
     if (cudaMalloc(&c->lim_counts, 2 * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->rate_cand, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->status_cand, sizeof(uint32_t)) != cudaSuccess)
@@ -557,7 +560,7 @@ void ader_destroy(ader_ctx* c) {
                   (void*)c->lim_flags, (void*)c->lim_list, (void*)c->fix_list, (void*)c->nbr,
                   (void*)c->force, (void*)c->lim_counts, (void*)c->rate_cand,
                   (void*)c->status_cand, (void*)c->corr_cells, (void*)c->plan_dev,
-                  (void*)c->kids_dev})
+                  (void*)c->kids_dev, (void*)c->fv_scratch})
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev_chunk)
     if (e) cudaEventDestroy(e);

@@ -125,6 +125,7 @@ struct LimiterArgs {
   double gamma, delta0, eps;
   unsigned long long* rate_max;
   uint32_t* status;
+  double* fv_scratch;      // 3D N >= 6: global scratch slots of the FV kernel's CTAs
   double inv_h[kMaxLevels][3];
   BasisTables B;
   SubcellTables T;
@@ -132,13 +133,15 @@ struct LimiterArgs {
 
 enum class LimiterKernel { kBounds = 0, kDetect = 1, kFV = 2, kFix = 3 };
 
-// Limiter kernels exist for 2D orders 1..7 and 3D orders 1..5 (pde 0 Euler,
-// 1 acoustics); `grid` is the CTA count of the kFV and kFix kernels, which
-// loop over the device-side lists.
+// Limiter kernels for orders 1..7 (pde 0 Euler, 1 acoustics); `grid` is the
+// CTA count of the kFV and kFix kernels, which loop over the device-side
+// lists.  In 3D at orders 6 and 7 the FV kernel needs
+// limiter_fv_scratch_3d(order, pde) doubles of global scratch per CTA.
 cudaError_t launch_limiter_2d(int order, int pde, LimiterKernel which, const LimiterArgs& a, int grid,
                               cudaStream_t s);
 cudaError_t launch_limiter_3d(int order, int pde, LimiterKernel which, const LimiterArgs& a, int grid,
                               cudaStream_t s);
+int64_t limiter_fv_scratch_3d(int order, int pde);
 
 enum class Precision { kFP64 = 0, kFP32 = 1, kTF32 = 2, kTF32x3 = 3, kBF16x3 = 4, kDF64 = 5 };
 

@@ -273,6 +273,12 @@ struct FvSmem {
   static constexpr int recon = DIM == 2 ? M * L::S * L::n : M * (L::S * L::S * L::n + L::S * L::n * L::n);
   static constexpr int X = (proj > recon ? proj : recon) > H ? (proj > recon ? proj : recon) : H;
   static constexpr int doubles = tables + V + H + X;
+  // A patch that does not fit one CTA's shared memory (3D, N >= 6) keeps V,
+  // the new averages Vn, H and X in a global scratch slot of this CTA (L2
+  // resident: a few hundred KB per CTA); shared memory then holds the tables.
+  static constexpr bool kBig = size_t(doubles) * 8 > 200 * 1024;
+  static constexpr int slot = kBig ? 2 * V + H + X : 0;   // doubles of global scratch per CTA
+  static constexpr int smem = kBig ? tables : doubles;
 };
 
 // Rusanov flux between states with a local speed.
@@ -301,9 +307,10 @@ __global__ void __launch_bounds__(256) limiter_fv_kernel(const LimiterArgs a) {
   double* sR = sA + S * n;
   double* sPi = sR + S * n;
   double* red = sPi + S * n;
-  double* V = smem + SM::tables;
+  double* V = SM::kBig ? a.fv_scratch + size_t(blockIdx.x) * SM::slot : smem + SM::tables;
   double* H = V + SM::V;
   double* X = H + SM::H;
+  double* Vn = X + SM::X;  // kBig: new averages (else they stay in registers)
   double* G = X;  // face fluxes reuse the scratch between projection and reconstruction
   load_tables<N>(a.T, sA, sR, sPi);
   __syncthreads();
@@ -371,11 +378,13 @@ __global__ void __launch_bounds__(256) limiter_fv_kernel(const LimiterArgs a) {
       __syncthreads();
     }
     // first-order FV update of every subcell; boundary subface fluxes to G
-    double vnew[PER][M];
+    constexpr int PR = SM::kBig ? 1 : PER;  // register slots for the new values
+    double vnew[PR][M];
     double rate = 0.0;
-#pragma unroll
+#pragma unroll(SM::kBig ? 1 : PER)
     for (int p = 0; p < PER; ++p) {
       const int sub = threadIdx.x + p * L::THREADS;
+      const int pr = SM::kBig ? 0 : p;
       if (sub < SS) {
         const int sid[3] = {sub % S, (sub / S) % S, sub / (S * S)};
         double q[M], dv[M];
@@ -411,13 +420,16 @@ __global__ void __launch_bounds__(256) limiter_fv_kernel(const LimiterArgs a) {
             for (int v = 0; v < M; ++v) G[((2 * dr + 1) * M + v) * SF + tan] = FR[v];
         }
 #pragma unroll
-        for (int v = 0; v < M; ++v) vnew[p][v] = q[v] + dv[v];
+        for (int v = 0; v < M; ++v) vnew[pr][v] = q[v] + dv[v];
+        if constexpr (SM::kBig)
+#pragma unroll
+          for (int v = 0; v < M; ++v) Vn[v * SS + sub] = vnew[pr][v];
         double r = 0.0;
         bool ok_all = true;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           bool ok;
-          r += PDE::max_speed(vnew[p], d, a.gamma, &ok) * a.inv_h[lv][d];
+          r += PDE::max_speed(vnew[pr], d, a.gamma, &ok) * a.inv_h[lv][d];
           ok_all = ok_all && ok;
         }
         if (!ok_all) atomicOr(a.status, kStatusNonPhysical);
@@ -425,12 +437,16 @@ __global__ void __launch_bounds__(256) limiter_fv_kernel(const LimiterArgs a) {
       }
     }
     __syncthreads();
+    if constexpr (SM::kBig) {
+      for (int t = threadIdx.x; t < M * SS; t += blockDim.x) V[t] = Vn[t];
+    } else {
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int sub = threadIdx.x + p * L::THREADS;
-      if (sub < SS)
+      for (int p = 0; p < PER; ++p) {
+        const int sub = threadIdx.x + p * L::THREADS;
+        if (sub < SS)
 #pragma unroll
-        for (int v = 0; v < M; ++v) V[v * SS + sub] = vnew[p][v];
+          for (int v = 0; v < M; ++v) V[v * SS + sub] = vnew[p][v];
+      }
     }
     rate = block_reduce(rate, true, red);
     if (threadIdx.x == 0) {
@@ -533,6 +549,10 @@ __global__ void __launch_bounds__(256) limiter_fix_kernel(const LimiterArgs a) {
   }
 }
 
+// Doubles of global scratch per CTA the FV kernel needs (0: shared memory only).
+template <int DIM, int N, int M>
+constexpr int fv_scratch_slot() { return FvSmem<DIM, N, M>::slot; }
+
 template <int DIM, int N, class PDE>
 cudaError_t launch_limiter_t(LimiterKernel which, const LimiterArgs& a, int grid, cudaStream_t s) {
   using L = LimShape<DIM, N>;
@@ -554,7 +574,8 @@ cudaError_t launch_limiter_t(LimiterKernel which, const LimiterArgs& a, int grid
     else
       limiter_detect_kernel<DIM, N, PDE><<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
   } else if (which == LimiterKernel::kFV) {
-    const size_t bytes = sizeof(double) * size_t(FvSmem<DIM, N, M>::doubles);
+    const size_t bytes = sizeof(double) * size_t(FvSmem<DIM, N, M>::smem);
+    if (FvSmem<DIM, N, M>::kBig && !a.fv_scratch) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
       cudaFuncSetAttribute(limiter_fv_kernel<DIM, N, PDE>,

@@ -48,7 +48,7 @@ def limited_step_parity(solver, om, perm, u0, P, B, force=None, steps=1):
     return outs
 
 
-@pytest.mark.parametrize("dim,order,base", [(2, 3, 4), (2, 7, 3), (3, 2, 3), (3, 5, 3)])
+@pytest.mark.parametrize("dim,order,base", [(2, 3, 4), (2, 7, 3), (3, 2, 3), (3, 5, 3), (3, 7, 3)])
 def test_all_cells_limited(dim, order, base):
     solver, om, perm = build_pair(dim, order, "euler", base, 0, limiter=True)
     B = obasis.Basis(order)
@@ -60,8 +60,9 @@ def test_all_cells_limited(dim, order, base):
 
 
 @pytest.mark.parametrize("dim,order,base,pde", [(2, 3, 6, "euler"), (3, 3, 3, "euler"),
-                                                (3, 5, 3, "euler"), (2, 4, 5, "acoustics"),
-                                                (3, 2, 3, "acoustics")])
+                                                (3, 5, 3, "euler"), (3, 6, 3, "euler"),
+                                                (2, 4, 5, "acoustics"), (3, 2, 3, "acoustics"),
+                                                (3, 7, 3, "acoustics")])
 def test_forced_subset_conserves(dim, order, base, pde):
     solver, om, perm = build_pair(dim, order, pde, base, 0, limiter=True)
     B = obasis.Basis(order)
@@ -105,13 +106,13 @@ def test_explosion_detection(dim, order, base, steps):
     assert solver.status() == 0
 
 
-def test_limiter_off_by_default_and_guarded():
+def test_limiter_off_by_default():
     from paper_1806_07984_gb300 import Solver, ader as A
     s = Solver(2, 3, "euler", base=(3, 3, 1), cfl=workloads.ADER_CFL[3])
     with pytest.raises(A.AderError):
         s.limiter_flags()
     with pytest.raises(A.AderError):
-        Solver(3, 6, "euler", base=(3, 3, 3), cfl=workloads.ADER_CFL[6], limiter=True)
+        s.force_limit(np.ones(9, dtype=bool))
 
 
 def test_pipeline_chunks_do_not_change_the_result():

@@ -114,8 +114,8 @@ def test_mesh_bad_arguments(A):
 
 
 def test_config_rejected_before_any_device_call(A):
-    """ader_init validates the configuration on the host: unsupported limiter
-    orders and malformed limiter flags return ADER_ERR_ARG without a GPU."""
+    """ader_init validates the configuration on the host: malformed limiter
+    and pipeline settings return ADER_ERR_ARG without a GPU."""
     def cfg(dim, order, limiter):
         c = A.ader_config()
         c.dim, c.order, c.nvar, c.pde = dim, order, dim + 2, A.ADER_EULER
@@ -124,7 +124,11 @@ def test_config_rejected_before_any_device_call(A):
             c.base[d], c.lo[d], c.hi[d] = 3, 0.0, 1.0
         c.limiter = limiter
         return c
-    for bad in (cfg(3, 6, 1), cfg(3, 7, 1), cfg(2, 3, 2)):
+    bad_chunks = cfg(3, 3, 0)
+    bad_chunks.pipeline_chunks = 65
+    bad_ctas = cfg(3, 3, 0)
+    bad_ctas.pipeline_ctas = -1
+    for bad in (cfg(2, 3, 2), cfg(3, 3, -1), bad_chunks, bad_ctas):
         with pytest.raises(A.AderError) as e:
             A.ader_init(bad)
         assert e.value.status == -1
