@@ -271,6 +271,15 @@ ader_status ader_limiter_flags(ader_ctx* ctx, uint32_t* flags, int on_device, in
  * clears it too.  ADER_ERR_ARG when the context has no limiter. */
 ader_status ader_limiter_force(ader_ctx* ctx, const uint8_t* force);
 
+/* Remesh flags that follow the shocks (the paper refines the DG solution down
+ * to the FV level near shocks, so that adaptivity never cuts through an FV
+ * region): flags[c] = +1 for the cells that were troubled in the last
+ * corrector (limited or kept at a transition) and their face neighbours, when
+ * below max_level; -1 for every other cell above level 0; else 0.  Host array,
+ * one entry per cell in mesh order, for ader_remesh.  Synchronises.
+ * ADER_ERR_ARG when the context has no limiter. */
+ader_status ader_limiter_refine_flags(ader_ctx* ctx, int8_t* flags);
+
 /* Discrete adjoint of one step: *lambda_out = A^T lambda_in, where A is the
  * linear map u(T) -> u(T+dt) of ader_step/ader_predict+ader_riemann+
  * ader_correct for linear acoustics (ADER_ACOUSTICS) with the dt stored at

@@ -35,7 +35,11 @@ Readings where the paper is silent:
   of the FV regions): a troubled cell with a non-conforming face keeps its DG
   candidate and is reported as such;
 * the next time step comes from the final state: the nodes of every cell and
-  the subcell averages of the limited cells.
+  the subcell averages of the limited cells;
+* refinement around the shocks (the paper refines the DG solution down to the
+  FV level near shocks, so that no adaptivity cuts through an FV region):
+  +1 for troubled cells and their face neighbours below the finest level, -1
+  for every other cell above the base level.
 """
 from dataclasses import dataclass
 
@@ -229,3 +233,36 @@ def step_limited(mesh, u, dt, pde, B, iters=None, force=None, predictor="picard"
         from .stability import cfl_number
         cfl = cfl_number(B.order)
     return LimitedStep(u_new, cand, limited, kept, fixed, Fs, cfl / rate)
+
+
+def face_neighbours(mesh):
+    """Face-neighbour leaves of every cell: the conforming neighbour, the finer
+    cells across a parent face, the coarser cell across a child face."""
+    conf, parents = mesh.faces()
+    nb = [set() for _ in mesh.cells]
+    for L, R, _ in conf:
+        nb[L].add(R)
+        nb[R].add(L)
+    for coarse, _, _, kids in parents:
+        for f, _ in kids:
+            nb[coarse].add(f)
+            nb[f].add(coarse)
+    return nb
+
+
+def refine_flags(mesh, troubled):
+    """Remesh flags that bring troubled cells and their face neighbours to the
+    finest level and coarsen everything else."""
+    troubled = np.asarray(troubled, dtype=bool)
+    mark = troubled.copy()
+    nb = face_neighbours(mesh)
+    for c in np.flatnonzero(troubled):
+        for j in nb[c]:
+            mark[j] = True
+    flags = np.zeros(len(mesh.cells), dtype=np.int8)
+    for i, (lvl, _) in enumerate(mesh.cells):
+        if mark[i] and lvl < mesh.max_level:
+            flags[i] = 1
+        elif not mark[i] and lvl > 0:
+            flags[i] = -1
+    return flags

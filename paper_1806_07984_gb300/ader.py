@@ -39,7 +39,7 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
            "ader_batch_status_word", "ader_batch_launch_count", "ader_adjoint_step",
            "ader_sample", "ader_sample_adjoint", "ader_gradient_flags", "ader_limiter_flags",
-           "ader_limiter_force"]
+           "ader_limiter_force", "ader_limiter_refine_flags"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -103,6 +103,7 @@ def lib():
         "ader_launch_count": ([_vp, _i64p], ctypes.c_int),
         "ader_limiter_flags": ([_vp, _vp, ctypes.c_int, _i64p, _vp], ctypes.c_int),
         "ader_limiter_force": ([_vp, _vp], ctypes.c_int),
+        "ader_limiter_refine_flags": ([_vp, _vp], ctypes.c_int),
         "ader_mesh_create": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
         "ader_mesh_destroy": ([_vp], None),
         "ader_mesh_adapt": ([_vp, _vp], ctypes.c_int),
@@ -278,6 +279,13 @@ def ader_limiter_force(ctx, force):
         return
     f = np.ascontiguousarray(np.asarray(force).astype(np.uint8))
     _check(ctx, lib().ader_limiter_force(ctx, _ptr(f)), "ader_limiter_force")
+
+
+def ader_limiter_refine_flags(ctx):
+    """Remesh flags around the cells troubled in the last corrector."""
+    out = np.zeros(ader_mesh_info(ctx)[0], dtype=np.int8)
+    _check(ctx, lib().ader_limiter_refine_flags(ctx, _ptr(out)), "ader_limiter_refine_flags")
+    return out
 
 
 def ader_launch_count(ctx):

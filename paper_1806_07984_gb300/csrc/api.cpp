@@ -1006,6 +1006,18 @@ ader_status ader_limiter_force(ader_ctx* c, const uint8_t* force) {
   return ADER_OK;
 }
 
+ader_status ader_limiter_refine_flags(ader_ctx* c, int8_t* flags) {
+  if (!c || !c->cfg.limiter || !flags) return ADER_ERR_ARG;
+  const size_t C = c->tree.cells.size();
+  std::vector<uint32_t> lf(C);
+  CK(cudaDeviceSynchronize(), "sync before limiter flags");
+  if (C) CK(cudaMemcpy(lf.data(), c->lim_flags, sizeof(uint32_t) * C, cudaMemcpyDeviceToHost), "limiter flags");
+  std::vector<uint8_t> troubled(C);
+  for (size_t i = 0; i < C; ++i) troubled[i] = (lf[i] & (kLimited | kKeptAtTransition)) ? 1 : 0;
+  c->tree.refine_around(troubled.data(), flags);
+  return ADER_OK;
+}
+
 ader_status ader_launch_count(ader_ctx* c, int64_t* out) {
   if (!c || !out) return ADER_ERR_ARG;
   *out = c->launches;

@@ -264,6 +264,28 @@ void Tree::classify(const int8_t* refine_flags) {
   for (size_t i = 0; i < n; ++i) corr_cells[size_t(fill[size_t(ready[i] + 1)]++)] = int32_t(i);
 }
 
+void Tree::refine_around(const uint8_t* troubled, int8_t* flags) const {
+  const size_t n = cells.size();
+  std::vector<uint8_t> mark(troubled, troubled + n);
+  for (const ConfFace& f : conf_all) {
+    if (troubled[size_t(f.left)]) mark[size_t(f.right)] = 1;
+    if (troubled[size_t(f.right)]) mark[size_t(f.left)] = 1;
+  }
+  const size_t S = dim_ == 3 ? 9 : 3;
+  for (size_t p = 0; p < parents.size(); ++p) {
+    const size_t coarse = size_t(parents[p].coarse);
+    for (size_t s = 0; s < S; ++s) {
+      const size_t fine = size_t(child_fine[p * S + s]);
+      if (troubled[coarse]) mark[fine] = 1;
+      if (troubled[fine]) mark[coarse] = 1;
+    }
+  }
+  for (size_t i = 0; i < n; ++i) {
+    const int lv = cells[i].level;
+    flags[i] = mark[i] ? (lv < max_level_ ? 1 : 0) : (lv > 0 ? -1 : 0);
+  }
+}
+
 void Tree::set_chunks(int K) {
   chunks = std::max(1, K);
   std::vector<int8_t> flags(cells.size(), 0);

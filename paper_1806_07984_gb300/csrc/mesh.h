@@ -177,6 +177,12 @@ class Tree {
   bool remesh(const int8_t* flags, std::vector<TransferItem>* plan,
               std::vector<int32_t>* coarsen_children);
 
+  // Refinement around troubled cells (limiter): +1 for cells with
+  // troubled[c] != 0 and their face neighbours (conforming, finer across a
+  // parent face, coarser across a child face) below max_level, -1 for every
+  // other cell above level 0.
+  void refine_around(const uint8_t* troubled, int8_t* flags) const;
+
   // Geometric criterion around a ball (periodic distance): refine leaves
   // below max_level whose box meets the ball, coarsen leaves above level 0
   // whose parent's box misses it.

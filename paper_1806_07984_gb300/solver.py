@@ -160,6 +160,10 @@ class Solver:
         bit 0 limited, bit 1 face flux replaced, bit 2 kept at a transition."""
         return A.ader_limiter_flags(self.ctx, self._stream(None))
 
+    def limiter_refine_flags(self):
+        """Remesh flags that refine around the last step's troubled cells."""
+        return A.ader_limiter_refine_flags(self.ctx)
+
     def force_limit(self, mask):
         """Treat the cells in ``mask`` as troubled in the following steps
         (None clears)."""

@@ -141,3 +141,38 @@ def test_pipeline_chunks_do_not_change_the_result():
         assert np.array_equal(r[0], results[0][0]) and r[1] == results[0][1]
     assert np.array_equal(results[4][0], results[3][0]) and results[4][1] == results[3][1]
     assert not np.array_equal(results[3][0], results[0][0])   # the limiter acted
+
+
+def test_refinement_follows_the_shock():
+    """Limited steps with a remesh after each that refines around the
+    troubled cells (and coarsens elsewhere): flags, meshes and states equal
+    the oracle's."""
+    from gpu_helpers import lib_keys
+    solver, om, perm = build_pair(2, 3, "euler", 27, 1, limiter=True)
+    B = obasis.Basis(3)
+    P = opde.Euler(2)
+    X = om.node_coords(B.xi)
+    u = np.ascontiguousarray(np.moveaxis(workloads.circular_explosion(X, width=0.02), 0, 1))
+    solver.set_state(u[perm])
+    for cycle in range(3):
+        h = om.cell_widths()
+        dt = oader.cfl_dt(u, h, P, 3)
+        solver.compute_dt()
+        assert abs(solver.dt.item() - dt) < TOL * dt
+        ref = olim.step_limited(om, u, dt, P, B)
+        solver.step(1)
+        assert rel_l2(solver.get_state().cpu().numpy(), ref.u[perm]) < TOL
+        fl_ref = olim.refine_flags(om, ref.limited | ref.kept)
+        fl_gpu = solver.limiter_refine_flags()
+        assert np.array_equal(fl_gpu, fl_ref[perm])
+        troubled = ref.limited | ref.kept
+        assert troubled.any() and (fl_ref[troubled] >= 0).all()
+        if cycle == 0:
+            assert (fl_ref > 0).any()
+        u = om.remesh(ref.u, fl_ref, B)
+        solver.remesh(fl_gpu)
+        keys = lib_keys(solver)
+        assert sorted(keys) == om.cells
+        perm = np.array([om.index[k] for k in keys])
+        assert rel_l2(solver.get_state().cpu().numpy(), u[perm]) < TOL
+    assert max(k[0] for k in om.cells) == 1

@@ -250,3 +250,28 @@ def test_explosion_limits_near_the_shock():
         assert np.isfinite(out.u).all() and (out.u[:, 0] > 0).all()
         assert (P.pressure(np.moveaxis(out.u, 1, 0)) > 0).all()
         u, dt = out.u, out.dt_next
+
+
+def test_refine_flags_around_troubled_cells():
+    """Troubled cells and their face neighbours (across transitions too) are
+    refined below the finest level; every other cell above level 0 coarsens."""
+    m = refined_mesh(2, 9, 2, (0.5, 0.5), 0.1, rounds=1)
+    troubled = np.zeros(len(m.cells), dtype=bool)
+    levels = np.array([k[0] for k in m.cells])
+    c0 = int(np.flatnonzero(levels == 1)[0])
+    c1 = int(np.flatnonzero(levels == 0)[0])
+    troubled[[c0, c1]] = True
+    flags = lim.refine_flags(m, troubled)
+    nb = lim.face_neighbours(m)
+    marked = set([c0, c1]) | nb[c0] | nb[c1]
+    for i, (lvl, _) in enumerate(m.cells):
+        if i in marked:
+            assert flags[i] == (1 if lvl < m.max_level else 0)
+        else:
+            assert flags[i] == (-1 if lvl > 0 else 0)
+    # a level-1 cell at the transition has its coarse neighbour among its face neighbours
+    trans = [i for i in range(len(m.cells)) if levels[i] == 1 and any(levels[j] == 0 for j in nb[i])]
+    assert trans
+    # symmetric neighbour relation, 2d faces per cell at least
+    for i in range(len(m.cells)):
+        assert all(i in nb[j] for j in nb[i]) and len(nb[i]) >= 4
