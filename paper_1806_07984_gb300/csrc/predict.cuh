@@ -340,6 +340,20 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
         for (int v = 0; v < M; ++v) {
           const Real* line = my_fb + (d * M + v) * NS + base;
+          if constexpr (kDinRegs && n % 2 == 0) {
+            // FP32 x-lines are contiguous and 8-byte aligned (they start at a
+            // multiple of n): two elements per shared-memory load
+            if (d == 0) {
+              const float2* l2 = reinterpret_cast<const float2*>(line);
+#pragma unroll
+              for (int j2 = 0; j2 < n / 2; ++j2) {
+                const float2 p = l2[j2];
+                g[v] = fma(Dr[0][2 * j2], p.x, g[v]);
+                g[v] = fma(Dr[0][2 * j2 + 1], p.y, g[v]);
+              }
+              continue;
+            }
+          }
 #pragma unroll
           for (int j = 0; j < n; ++j) {
             Real dj;
