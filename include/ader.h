@@ -116,7 +116,7 @@ typedef struct {
   ader_precision prec;
   ader_predictor predictor;  /* ADER_PREDICTOR_CK: acoustics, FP64 or FP32 */
   int limiter;               /* 1: a posteriori subcell FV limiter in every corrector
-                                (2D orders 1..7, 3D orders 1..5); see ader_limiter_flags */
+                                (orders 1..7, 2D and 3D); see ader_correct, ader_limiter_flags */
   double limiter_delta0;     /* relaxed maximum principle: delta = max(delta0, eps (max - min)); */
   double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
   int pipeline_chunks;       /* ader_step: enclave chunks K (0 selects 8, 1 disables); see ader_step */
