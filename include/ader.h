@@ -417,6 +417,21 @@ ader_status ader_mesh_faces(ader_mesh* mesh, int32_t* conf_out, int32_t* parents
 ader_status ader_mesh_sphere_flags(ader_mesh* mesh, const double center[3], double radius,
                                    const double lo[3], const double hi[3], int8_t* flags);
 
+/* The remesh rule of ader_limiter_refine_flags for a given troubled set
+ * (troubled[c] != 0, one byte per cell in mesh order). */
+ader_status ader_mesh_refine_around(ader_mesh* mesh, const uint8_t* troubled, int8_t* flags);
+
+/* The enclave pipeline of ader_step for K chunks (see ader_step) on the host
+ * mesh, whose skeleton is its transition cells: fills chunk_off[K+1]
+ * (enclave cell ranges in ader_mesh_leaves order), face_off[K+1]
+ * (conforming faces after the skeleton ones, per chunk), corr_off[K+2] and
+ * corr_cells[ncells] (cells grouped by the stage that completes their faces),
+ * and conf_out[3 * nconf] (left, right, dir in pipeline order); *nskel_faces
+ * receives the number of skeleton conforming faces.  Every output may be NULL. */
+ader_status ader_mesh_pipeline(ader_mesh* mesh, int K, int64_t* chunk_off, int64_t* face_off,
+                               int64_t* corr_off, int32_t* corr_cells, int32_t* conf_out,
+                               int64_t* nskel_faces);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,8 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
            "ader_batch_status_word", "ader_batch_launch_count", "ader_adjoint_step",
            "ader_sample", "ader_sample_adjoint", "ader_gradient_flags", "ader_limiter_flags",
-           "ader_limiter_force", "ader_limiter_refine_flags"]
+           "ader_limiter_force", "ader_limiter_refine_flags", "ader_mesh_refine_around",
+           "ader_mesh_pipeline"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -104,6 +105,8 @@ def lib():
         "ader_limiter_flags": ([_vp, _vp, ctypes.c_int, _i64p, _vp], ctypes.c_int),
         "ader_limiter_force": ([_vp, _vp], ctypes.c_int),
         "ader_limiter_refine_flags": ([_vp, _vp], ctypes.c_int),
+        "ader_mesh_refine_around": ([_vp, _vp, _vp], ctypes.c_int),
+        "ader_mesh_pipeline": ([_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _i64p], ctypes.c_int),
         "ader_mesh_create": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
         "ader_mesh_destroy": ([_vp], None),
         "ader_mesh_adapt": ([_vp, _vp], ctypes.c_int),
@@ -461,3 +464,25 @@ def ader_gradient_flags(ctx, var, refine_above, coarsen_below):
     _check(ctx, lib().ader_gradient_flags(ctx, var, float(refine_above), float(coarsen_below),
                                           _ptr(eta), _ptr(flags)), "ader_gradient_flags")
     return eta, flags
+
+
+def ader_mesh_refine_around(mesh, troubled):
+    t = np.ascontiguousarray(np.asarray(troubled).astype(np.uint8))
+    out = np.zeros(len(t), dtype=np.int8)
+    _check(None, lib().ader_mesh_refine_around(mesh, _ptr(t), _ptr(out)), "ader_mesh_refine_around")
+    return out
+
+
+def ader_mesh_pipeline(mesh, K):
+    """(chunk_off, face_off, corr_off, corr_cells, conf, n_skeleton_faces) of
+    the enclave pipeline with K chunks."""
+    C, _, nconf, _ = ader_mesh_sizes(mesh)
+    chunk = np.zeros(K + 1, dtype=np.int64)
+    face = np.zeros(K + 1, dtype=np.int64)
+    corr = np.zeros(K + 2, dtype=np.int64)
+    cells = np.zeros(C, dtype=np.int32)
+    conf = np.zeros((nconf, 3), dtype=np.int32)
+    nsk = ctypes.c_int64()
+    _check(None, lib().ader_mesh_pipeline(mesh, K, _ptr(chunk), _ptr(face), _ptr(corr), _ptr(cells),
+                                          _ptr(conf), ctypes.byref(nsk)), "ader_mesh_pipeline")
+    return chunk, face, corr, cells, conf, nsk.value

@@ -1106,4 +1106,30 @@ ader_status ader_mesh_sphere_flags(ader_mesh* m, const double center[3], double 
   return ADER_OK;
 }
 
+ader_status ader_mesh_refine_around(ader_mesh* m, const uint8_t* troubled, int8_t* flags) {
+  if (!m || !troubled || !flags) return ADER_ERR_ARG;
+  m->tree.refine_around(troubled, flags);
+  return ADER_OK;
+}
+
+ader_status ader_mesh_pipeline(ader_mesh* m, int K, int64_t* chunk_off, int64_t* face_off,
+                               int64_t* corr_off, int32_t* corr_cells, int32_t* conf_out,
+                               int64_t* nskel_faces) {
+  if (!m || K < 1 || K > 64) return ADER_ERR_ARG;
+  Tree& t = m->tree;
+  t.set_chunks(K);
+  if (chunk_off) std::copy(t.chunk_off.begin(), t.chunk_off.end(), chunk_off);
+  if (face_off) std::copy(t.face_off.begin(), t.face_off.end(), face_off);
+  if (corr_off) std::copy(t.corr_off.begin(), t.corr_off.end(), corr_off);
+  if (corr_cells) std::copy(t.corr_cells.begin(), t.corr_cells.end(), corr_cells);
+  if (conf_out)
+    for (size_t i = 0; i < t.conf.size(); ++i) {
+      conf_out[3 * i + 0] = t.conf[i].left;
+      conf_out[3 * i + 1] = t.conf[i].right;
+      conf_out[3 * i + 2] = t.conf[i].dir;
+    }
+  if (nskel_faces) *nskel_faces = t.n_conf_skeleton;
+  return ADER_OK;
+}
+
 }  // extern "C"

@@ -132,3 +132,71 @@ def test_config_rejected_before_any_device_call(A):
         with pytest.raises(A.AderError) as e:
             A.ader_init(bad)
         assert e.value.status == -1
+
+
+def _pair(A, dim, base, max_level, centers, radius):
+    om = omesh.Mesh(dim, (base,) * dim, max_level)
+    lm = A.ader_mesh_create(dim, (base,) * dim, max_level)
+    import oracle.basis as ob
+    for center in centers:
+        fl = omesh.sphere_flags(om, center, radius)
+        om.remesh(np.zeros((len(om.cells), 1) + (2,) * dim), fl, ob.Basis(1))
+        A.ader_mesh_adapt(lm, A.ader_mesh_sphere_flags(lm, center, radius))
+    keys = lib_mesh_state(A, lm, dim)[0]
+    assert sorted(keys) == om.cells
+    return om, lm, keys
+
+
+@pytest.mark.parametrize("dim,base,centers", [(2, 9, [(0.45, 0.55), (0.45, 0.55)]),
+                                              (3, 3, [(0.5, 0.5, 0.5), (0.5, 0.5, 0.5)])])
+def test_refine_around_matches_oracle(A, dim, base, centers):
+    """The limiter's remesh rule (troubled cells and their face neighbours
+    across transitions) equals the oracle's bit for bit."""
+    from oracle import limiter as olim
+    om, lm, keys = _pair(A, dim, base, 2, centers, 0.15)
+    try:
+        perm = np.array([om.index[k] for k in keys])
+        rng = np.random.default_rng(dim)
+        for _ in range(3):
+            troubled = rng.random(len(keys)) < 0.05
+            got = A.ader_mesh_refine_around(lm, troubled)
+            inv = np.argsort(perm)
+            want = olim.refine_flags(om, troubled[inv])
+            assert np.array_equal(got, want[perm])
+    finally:
+        A.ader_mesh_destroy(lm)
+
+
+@pytest.mark.parametrize("K", [1, 3, 8])
+def test_pipeline_lists(A, K):
+    """Enclave pipeline lists: chunks partition the enclave, every conforming
+    face sits after the skeleton faces in the stage of the later chunk of its
+    two cells, and every cell is corrected exactly once, in the stage after
+    which all its faces are solved."""
+    om, lm, keys = _pair(A, 3, 3, 2, [(0.5, 0.5, 0.5), (0.5, 0.5, 0.5)], 0.2)
+    try:
+        C = len(keys)
+        _, skel = A.ader_mesh_leaves(lm)
+        conf_all, par, kids = A.ader_mesh_faces(lm, 3)
+        chunk_off, face_off, corr_off, corr_cells, conf, nsk = A.ader_mesh_pipeline(lm, K)
+        encl = np.flatnonzero(skel == 0)
+        assert chunk_off[0] == 0 and chunk_off[-1] == len(encl) and (np.diff(chunk_off) >= 0).all()
+        chunk = -np.ones(C, dtype=int)
+        for k in range(K):
+            chunk[encl[chunk_off[k]:chunk_off[k + 1]]] = k
+        # faces: same set as the mesh's, skeleton faces first, then by stage
+        assert sorted(map(tuple, conf.tolist())) == sorted(map(tuple, conf_all.tolist()))
+        assert all(skel[a] and skel[b] for a, b, _ in conf[:nsk])
+        assert face_off[0] == 0 and face_off[-1] == len(conf) - nsk
+        ready = chunk.copy()
+        for k in range(K):
+            for a, b, _ in conf[nsk + face_off[k]:nsk + face_off[k + 1]]:
+                assert max(chunk[a], chunk[b]) == k
+                ready[a] = max(ready[a], k)
+                ready[b] = max(ready[b], k)
+        # cells: a permutation, grouped by ready stage + 1
+        assert sorted(corr_cells.tolist()) == list(range(C))
+        for g in range(K + 1):
+            assert all(ready[c] + 1 == g for c in corr_cells[corr_off[g]:corr_off[g + 1]])
+    finally:
+        A.ader_mesh_destroy(lm)
