@@ -621,7 +621,9 @@ def main():
     torch.cuda.synchronize()
     c0 = time.perf_counter()
     e2e_dofs = h2d = d2h = 0
+    e2e_each = []
     for i in range(e2e_steps):
+        t_i = time.perf_counter()
         s2.set_state(host)
         h2d += host.numel() * 8
         e2e_dofs += run_steps(s2, wl, 1, t_e2e, i)
@@ -629,13 +631,14 @@ def main():
             host = torch.empty(s2.state_shape(), dtype=torch.float64).pin_memory()
         A.ader_get_state(s2.ctx, host.data_ptr(), False, stream.cuda_stream)
         d2h += host.numel() * 8
+        e2e_each.append(round((time.perf_counter() - t_i) * 1e3, 1))
     torch.cuda.synchronize()
     e2e_time = time.perf_counter() - c0
     if world > 1:
         e2e_time, _ = reduce_over_ranks(torch, e2e_time, 0, device)
     e2e = {"value": e2e_dofs * world / e2e_time, "unit": "DoF-updates/s",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
-           "steps": e2e_steps, "host_cpus": f"{len(near)} CPUs local to the GPU" if near else "unbound"}
+           "steps": e2e_steps, "ms_each": e2e_each, "host_cpus": f"{len(near)} CPUs local to the GPU" if near else "unbound"}
     ncells, dofs_now, order, dim = s2.ncells, dofs_of(s2), s2.order, s2.dim
     s2.close()
 
