@@ -414,6 +414,100 @@ def run_limiter(torch, dim=2, order=3, base=729, steps=10, warmup=2):
     return out
 
 
+def ck_flops_per_cell(dim, order):
+    """Algorithmic flops of the Cauchy-Kowalevski predictor per cell (linear
+    acoustics, FMA = 2).  Per node: N time derivatives, each the derivatives
+    of the two nonzero flux components of every direction (2n each) and one
+    Taylor term per variable (2m); then the volume term (two nonzero
+    components per direction, 2n + 2 each) and u* = u + dt vol (2m).  Per face
+    node: Q-bar (m variables) and the two nonzero components of F-bar
+    extrapolated along the normal (2n each)."""
+    n, m = order + 1, dim + 1
+    NS, NF = n ** dim, n ** (dim - 1)
+    per_node = order * (dim * 2 * 2 * n + 2 * m) + dim * 2 * (2 * n + 2) + 2 * m
+    return NS * per_node + 2 * dim * NF * (m + 2) * 2 * n
+
+
+def run_ck(torch, order=4, base=54, steps=5, warmup=3):
+    """3D linear acoustics N=4 on a uniform periodic base^3 grid (eight seeded
+    Gaussian pressure pulses; base 54: the 0.63 GB state exceeds L2): the
+    forward step with the Cauchy-Kowalevski predictor against the Picard
+    predictor (N + 1 iterations), and the CK predictor kernel against the
+    FP64 ALU peak."""
+    from paper_1806_07984_gb300 import Solver
+    out = {}
+    finals = {}
+    for pred in ("ck", "picard"):
+        s = Solver(3, order, "acoustics", base=(base,) * 3, cfl=workloads.ADER_CFL[order],
+                   predictor=pred)
+        X = s.node_coords()
+        u0 = np.ascontiguousarray(np.moveaxis(workloads.acoustic_pulses(X, seed=1), 0, 1))
+        del X
+        s.set_state(torch.from_numpy(u0).cuda())
+        del u0
+        s.compute_dt()
+        s.step(warmup)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        dofs = s.ncells * s.nvar * s.n ** 3
+        finals[pred] = s.get_state()
+        t_pred = time_predictor(s, torch)
+        rec = {"value": dofs * steps / sec, "unit": "DoF-updates/s", "ms_per_step": sec / steps * 1e3,
+               "predictor_launch_ms": t_pred * 1e3, "status": s.status()}
+        if pred == "ck":
+            fl = ck_flops_per_cell(3, order) * s.ncells
+            achieved = fl / t_pred / 1e12
+            rec["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                               "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                               "algorithmic_flops": fl,
+                               "algorithmic_bytes": predictor_bytes_per_cell(3, order, s.nvar) * s.ncells}
+        out[pred] = rec
+        s.close()
+    d = finals["ck"] - finals["picard"]
+    out["ck_vs_picard_rel_l2"] = float(d.norm() / finals["picard"].norm())
+    del finals, d
+    out["workload"] = (f"3D acoustics N={order}, {base}^3 periodic, 8 Gaussian pulses (seed 1), "
+                       f"{steps} steps after {warmup}")
+    out["speedup"] = out["ck"]["value"] / out["picard"]["value"]
+    return out
+
+
+def run_indicator(s, torch, reps=5):
+    """The solution-based refinement indicator (ader_gradient_indicator, one
+    variable) on the bench mesh: device time per launch (CUDA events) against
+    the FP64 ALU peak, and the host-synchronous ader_gradient_flags call."""
+    from paper_1806_07984_gb300 import ader as A
+    st = torch.cuda.current_stream()
+    eta = torch.empty(s.ncells, dtype=torch.float64, device=s.device)
+    A.ader_gradient_indicator(s.ctx, 0, eta, st.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        A.ader_gradient_indicator(s.ctx, 0, eta, st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    n, NS = s.n, s.n ** s.dim
+    fl = s.ncells * NS * s.dim * (2 * n + 3)
+    by = s.ncells * (NS + 1) * 8
+    c0 = time.perf_counter()
+    s.gradient_flags(0, 1.0, 0.1)
+    t_flags = time.perf_counter() - c0
+    return {"launch_ms": t * 1e3, "cells_per_s": s.ncells / t,
+            "roofline": {"bound": "alu", "achieved": fl / t / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": fl / t / 1e12 / FP64_PEAK_TFLOPS,
+                         "algorithmic_flops": fl, "algorithmic_bytes": by, "hbm_gbs": by / t / 1e9},
+            "gradient_flags_call_ms": t_flags * 1e3,
+            "workload": "density derivative on the bench mesh (%d cells)" % s.ncells}
+
+
 def time_predictor(s, torch, reps=3):
     """Average duration of one ader_predict(ADER_ALL) launch, CUDA events on
     the launching stream."""
@@ -534,6 +628,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-limiter", action="store_true")
+    ap.add_argument("--no-ck", action="store_true")
+    ap.add_argument("--no-indicator", action="store_true")
     ap.add_argument("--pipeline", type=int, default=0,
                     help="enclave chunks per step (0 = library default, 1 = no pipelining)")
     ap.add_argument("--pipeline-ctas", type=int, default=0,
@@ -608,6 +704,8 @@ def main():
                 "kernel": kname,
                 "launch_ms": t_pred * 1e3, "algorithmic_flops": flops,
                 "algorithmic_bytes": bytes_, "hbm_gbs": bytes_ / t_pred / 1e9}
+
+    indicator = run_indicator(s, torch) if not args.no_indicator else None
 
     # ---- end to end through the public API with host buffers ---------------
     # Every step: H2D of the state from pinned host memory, one step, D2H of
@@ -716,6 +814,7 @@ def main():
                if (not args.no_adjoint and world == 1) else None)
     limiter = ({"2d_n3_729": run_limiter(torch, 2, 3, 729), "3d_n5_27": run_limiter(torch, 3, 5, 27, 5)}
                if (not args.no_limiter and world == 1) else None)
+    ck = run_ck(torch) if (not args.no_ck and world == 1) else None
 
 
     line = {"metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
@@ -737,7 +836,8 @@ def main():
                        "note": "host tree adaptation, list uploads, transfer kernel and skeleton "
                                "reclassification; the paper's timings exclude remeshing"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
-            "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter}
+            "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter,
+            "ck": ck, "indicator": indicator}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, seconds=10.0,

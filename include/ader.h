@@ -236,9 +236,17 @@ ader_status ader_remesh(ader_ctx* ctx, const int8_t* flags);
  * current state; flags[c] = +1 if eta > refine_above and the cell is below
  * max_level, -1 if eta < coarsen_below and the cell is above level 0, else 0.
  * eta_out (host, may be NULL) and flags (host) have one entry per cell in mesh
- * order.  Synchronises. */
+ * order.  Synchronises the device before and after. */
 ader_status ader_gradient_flags(ader_ctx* ctx, int var, double refine_above, double coarsen_below,
                                 double* eta_out, int8_t* flags);
+
+/* The indicator eta of ader_gradient_flags alone, on the device: eta_dev
+ * (device, caller-owned, ncells doubles, mesh order) receives eta[c] for
+ * variable var (0 <= var < nvar) from the current state, asynchronously on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  The caller
+ * orders it after the step that wrote the state (same stream, or an event).
+ * ADER_ERR_ARG for a bad var or a NULL eta_dev with cells present. */
+ader_status ader_gradient_indicator(ader_ctx* ctx, int var, double* eta_dev, void* stream);
 
 /* Skeleton batch: transition cells plus cells with flags[c] > 0 (flags may be
  * NULL).  Host call; uploads the new lists (synchronous). */

@@ -38,7 +38,8 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_batch_set_state", "ader_batch_get_state", "ader_batch_compute_dt",
            "ader_batch_get_dt", "ader_batch_set_launch", "ader_batch_tune", "ader_batch_run",
            "ader_batch_status_word", "ader_batch_launch_count", "ader_adjoint_step",
-           "ader_sample", "ader_sample_adjoint", "ader_gradient_flags", "ader_limiter_flags",
+           "ader_sample", "ader_sample_adjoint", "ader_gradient_flags", "ader_gradient_indicator",
+           "ader_limiter_flags",
            "ader_limiter_force", "ader_limiter_refine_flags", "ader_mesh_refine_around",
            "ader_mesh_pipeline"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
@@ -132,6 +133,7 @@ def lib():
         "ader_adjoint_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "ader_gradient_flags": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp],
                                 ctypes.c_int),
+        "ader_gradient_indicator": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
         "ader_sample": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
         "ader_sample_adjoint": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
                                 ctypes.c_int),
@@ -464,6 +466,13 @@ def ader_gradient_flags(ctx, var, refine_above, coarsen_below):
     _check(ctx, lib().ader_gradient_flags(ctx, var, float(refine_above), float(coarsen_below),
                                           _ptr(eta), _ptr(flags)), "ader_gradient_flags")
     return eta, flags
+
+
+def ader_gradient_indicator(ctx, var, eta_dev, stream=None):
+    """eta (device array of ncells doubles) of ader_gradient_flags, enqueued on
+    ``stream`` (a raw cudaStream_t handle; None = legacy default stream)."""
+    _check(ctx, lib().ader_gradient_indicator(ctx, var, _ptr(eta_dev), stream),
+           "ader_gradient_indicator")
 
 
 def ader_mesh_refine_around(mesh, troubled):

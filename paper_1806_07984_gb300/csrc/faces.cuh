@@ -469,14 +469,19 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::NS) transfer_kernel(cons
 }
 
 // Refinement indicator (epilogue of the corrector): per cell the largest
-// h |grad q| over its nodes, for one variable q.
+// h |grad q| over its nodes, for one variable q.  The nodes reduce |grad q|^2
+// (a tree maximum over the FP64 bit patterns, which order like the values for
+// non-negative doubles); the square root and h follow once per cell, which
+// gives the same value as taking them per node (both are monotone and
+// correctly rounded).
 template <int DIM, int N, int M>
 __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kernel(const IndicatorArgs a) {
   using SH = PredictShape<DIM, N>;
   constexpr int n = SH::n, NS = SH::NS, CPB = SH::CPB;
+  constexpr int kPow2 = pow2_ceil(NS);
   __shared__ double q[CPB][NS];
   __shared__ double sD[n * n];
-  __shared__ unsigned long long emax[CPB];
+  __shared__ unsigned long long r[CPB][NS];
   const int tid = threadIdx.x;
   const int cl = tid / NS;
   const int node = tid - cl * NS;
@@ -484,12 +489,11 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kerne
   const bool valid = cell < a.ncells;
   for (int t = tid; t < n * n; t += blockDim.x) sD[t] = a.B.D[t / n][t % n];
   q[cl][node] = valid ? a.u[(cell * M + a.var) * NS + node] : 0.0;
-  if (node == 0) emax[cl] = 0ull;
   __syncthreads();
   const int id[3] = {node % n, (node / n) % n, node / (n * n)};
   const int stride[3] = {1, n, n * n};
   const int lv = valid ? int(a.level[cell]) : 0;
-  double g2 = 0.0, hmax = 0.0;
+  double g2 = 0.0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int base = node - id[d] * stride[d];
@@ -498,12 +502,18 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kerne
     for (int j = 0; j < n; ++j) s = fma(sD[id[d] * n + j], q[cl][base + j * stride[d]], s);
     s *= a.inv_h[lv][d];
     g2 = fma(s, s, g2);
-    hmax = fmax(hmax, 1.0 / a.inv_h[lv][d]);
   }
-  const double eta = sqrt(g2) * hmax;
-  if (valid) atomicMax(&emax[cl], static_cast<unsigned long long>(__double_as_longlong(eta)));
-  __syncthreads();
-  if (valid && node == 0) a.eta[cell] = __longlong_as_double(static_cast<long long>(emax[cl]));
+  r[cl][node] = static_cast<unsigned long long>(__double_as_longlong(g2));
+  for (int st = kPow2 / 2; st > 0; st >>= 1) {
+    __syncthreads();
+    if (node < st && node + st < NS) r[cl][node] = r[cl][node] > r[cl][node + st] ? r[cl][node] : r[cl][node + st];
+  }
+  if (valid && node == 0) {
+    double hmax = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) hmax = fmax(hmax, 1.0 / a.inv_h[lv][d]);
+    a.eta[cell] = sqrt(__longlong_as_double(static_cast<long long>(r[cl][0]))) * hmax;
+  }
 }
 
 template <int DIM, int N, int M>

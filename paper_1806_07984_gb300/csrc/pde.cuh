@@ -16,6 +16,9 @@ struct Euler {
   static constexpr int M = DIM + 2;
   static constexpr bool kPositivity = true;
 
+  // Whether component v of f_d can be nonzero (Euler: every component).
+  __host__ __device__ static constexpr bool flux_nonzero(int, int) { return true; }
+
   // All DIM fluxes at one node.
   template <class R>
   __device__ __forceinline__ static void fluxes(const R (&q)[M], R (&f)[DIM][M], R gamma) {
@@ -78,6 +81,10 @@ struct Acoustics {
   static constexpr int DIM = DIM_;
   static constexpr int M = DIM + 1;
   static constexpr bool kPositivity = false;
+
+  // f_d has two nonzero components, p-row (v_d) and v_d-row (p); the kernels
+  // skip the contractions of the others (adding their zeros changes nothing).
+  __host__ __device__ static constexpr bool flux_nonzero(int d, int v) { return v == 0 || v == 1 + d; }
 
   template <class R>
   __device__ __forceinline__ static void fluxes(const R (&q)[M], R (&f)[DIM][M], R) {

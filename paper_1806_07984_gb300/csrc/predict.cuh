@@ -29,6 +29,8 @@
 namespace ader {
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+// Smallest power of two >= x (x >= 1).
+__host__ __device__ constexpr int pow2_ceil(int x) { return x <= 1 ? 1 : 2 * pow2_ceil((x + 1) / 2); }
 
 template <int DIM, int N>
 struct PredictShape {
@@ -311,7 +313,8 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
 #pragma unroll
-        for (int v = 0; v < M; ++v) my_fb[(d * M + v) * NS + node] = f[d][v];
+        for (int v = 0; v < M; ++v)
+          if (PDE::flux_nonzero(d, v)) my_fb[(d * M + v) * NS + node] = f[d][v];
     }
     __syncthreads();
 #pragma unroll
@@ -326,6 +329,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
         const Real* drow = &sDh[cl][d][idd * n];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
+          if (!PDE::flux_nonzero(d, v)) continue;
           const Real* line = line0 + v * NS;
 #pragma unroll
           for (int j = 0; j < n; ++j) g[v] = fma_acc(drow[j], line[j * sd], g[v]);
@@ -339,6 +343,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
         const int base = node - id[d] * stride[d];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
+          if (!PDE::flux_nonzero(d, v)) continue;
           const Real* line = my_fb + (d * M + v) * NS + base;
           if constexpr (kDinRegs && n % 2 == 0) {
             // FP32 x-lines are contiguous and 8-byte aligned (they start at a
@@ -483,6 +488,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   for (int d = 0; d < DIM; ++d)
 #pragma unroll
     for (int v = 0; v < M; ++v) {
+      if (!PDE::flux_nonzero(d, v)) continue;
       finite = finite && isfinite(Fb[d][v]);
       if (active) my_fb[(d * M + v) * NS + node] = Fb[d][v];
     }
@@ -496,6 +502,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     vol[v] = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
+      if (!PDE::flux_nonzero(d, v)) continue;
       const Real* Vrow = sV + id[d] * n;
       const Real* line = my_fb + (d * M + v) * NS + node - id[d] * stride[d];
       Real s = Real(0);
@@ -561,11 +568,12 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       for (int v = 0; v < M; ++v) {
         const Real* lq = my_qs + v * NS + base;
         const Real* lf = my_fb + (d * M + v) * NS + base;
+        const bool nz = PDE::flux_nonzero(d, v);
         Real sq = Real(0), sf = Real(0);
 #pragma unroll
         for (int j = 0; j < n; ++j) {
           sq = fma(phi[j], lq[j * stride[d]], sq);
-          sf = fma(phi[j], lf[j * stride[d]], sf);
+          if (nz) sf = fma(phi[j], lf[j * stride[d]], sf);
         }
         faceQ[fo + v * NF] = double(sq);
         faceF[fo + v * NF] = double(sf);

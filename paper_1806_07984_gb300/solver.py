@@ -145,6 +145,12 @@ class Solver:
     def gradient_flags(self, var, refine_above, coarsen_below):
         return A.ader_gradient_flags(self.ctx, var, refine_above, coarsen_below)
 
+    def gradient_indicator(self, var, stream=None):
+        """Device tensor eta[c] of gradient_flags, enqueued on ``stream``."""
+        eta = self.torch.empty(self.ncells, dtype=self.torch.float64, device=self.device)
+        A.ader_gradient_indicator(self.ctx, var, eta, self._stream(stream))
+        return eta
+
     def sphere_flags(self, center, radius):
         return A.ader_sphere_flags(self.ctx, center, radius)
 
