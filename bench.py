@@ -629,6 +629,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-limiter", action="store_true")
     ap.add_argument("--no-ck", action="store_true")
+    ap.add_argument("--section", choices=["ck", "limiter", "adjoint", "batched"], default=None,
+                    help="run one side section alone and print its JSON object (no headline)")
+    ap.add_argument("--ck-base", type=int, default=54, help="grid of the CK section (base^3)")
     ap.add_argument("--no-indicator", action="store_true")
     ap.add_argument("--pipeline", type=int, default=0,
                     help="enclave chunks per step (0 = library default, 1 = no pipelining)")
@@ -644,6 +647,17 @@ def main():
         return
 
     import torch
+    if args.section:
+        torch.cuda.set_device(0)
+        out = {"ck": lambda: run_ck(torch, base=args.ck_base),
+               "limiter": lambda: {"2d_n3_729": run_limiter(torch, 2, 3, 729),
+                                   "3d_n5_27": run_limiter(torch, 3, 5, 27, 5)},
+               "adjoint": lambda: {"picard": run_adjoint(torch, "picard"),
+                                   "ck": run_adjoint(torch, "ck")},
+               "batched": lambda: {"fp64": run_batched(torch, "fp64", 20, 2),
+                                   "fp32": run_batched(torch, "fp32", 20, 2)}}[args.section]()
+        print(json.dumps({"section": args.section, args.section: out}))
+        return
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -814,7 +828,7 @@ def main():
                if (not args.no_adjoint and world == 1) else None)
     limiter = ({"2d_n3_729": run_limiter(torch, 2, 3, 729), "3d_n5_27": run_limiter(torch, 3, 5, 27, 5)}
                if (not args.no_limiter and world == 1) else None)
-    ck = run_ck(torch) if (not args.no_ck and world == 1) else None
+    ck = run_ck(torch, base=args.ck_base) if (not args.no_ck and world == 1) else None
 
 
     line = {"metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,

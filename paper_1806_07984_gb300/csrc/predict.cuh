@@ -109,6 +109,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   constexpr int n = S::n, NS = S::NS, NF = S::NF, CPB = S::CPB, M = PDE::M;
   // sDh[c][d]: D scaled by 1/h_d of cell c; sMd = -dt Mt; sRs[k] = sum_l sMd[k][l]
   __shared__ Real sDh[CPB][DIM][n * n], sMd[n * n], sRs[n], sV[n * n], sw[n], sp0[n], sp1[n];
+  __shared__ Real sCk[n];  // Cauchy-Kowalevski: sCk[k] = dt^k / (k + 1)!
   // fb[CPB][DIM][M][NS] fluxes of one slice (later F-bar); qs[CPB][M][NS] Q-bar
   Real* fb = reinterpret_cast<Real*>(smem_raw);
   Real* qs = fb + CPB * DIM * M * NS;
@@ -127,6 +128,15 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     sw[tid] = Real(B.w[tid]);
     sp0[tid] = Real(B.phi0[tid]);
     sp1[tid] = Real(B.phi1[tid]);
+  }
+  if (SCHEME == 1 && tid == 0) {
+    // one thread forms the Taylor weights (a division each) for the CTA
+    Real c = Real(1);
+    sCk[0] = c;
+    for (int k = 1; k <= N; ++k) {
+      c = c * Real(dt) / Real(k + 1);
+      sCk[k] = c;
+    }
   }
 
   const int cl = active ? tid / NS : 0;
@@ -338,12 +348,18 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
       for (int v = 0; v < M; ++v) g[v] = settle(g[v]);
     } else {
+      // Sparse fluxes (few nonzero components per direction) leave few
+      // independent sums per node; there each (d, v) gets its own partial
+      // sum, added over d at the end, which shortens the dependent FMA chains.
+      Real part[DIM][M];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int base = node - id[d] * stride[d];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
           if (!PDE::flux_nonzero(d, v)) continue;
+          Real& acc = PDE::kSparseFlux ? part[d][v] : g[v];
+          if (PDE::kSparseFlux) acc = Real(0);
           const Real* line = my_fb + (d * M + v) * NS + base;
           if constexpr (kDinRegs && n % 2 == 0) {
             // FP32 x-lines are contiguous and 8-byte aligned (they start at a
@@ -353,8 +369,8 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
               for (int j2 = 0; j2 < n / 2; ++j2) {
                 const float2 p = l2[j2];
-                g[v] = fma(Dr[0][2 * j2], p.x, g[v]);
-                g[v] = fma(Dr[0][2 * j2 + 1], p.y, g[v]);
+                acc = fma(Dr[0][2 * j2], p.x, acc);
+                acc = fma(Dr[0][2 * j2 + 1], p.y, acc);
               }
               continue;
             }
@@ -371,9 +387,16 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
               jj = j + rz;
               jj = jj >= n ? jj - n : jj;
             }
-            g[v] = fma(dj, line[jj * stride[d]], g[v]);
+            acc = fma(dj, line[jj * stride[d]], acc);
           }
         }
+      }
+      if constexpr (PDE::kSparseFlux) {
+#pragma unroll
+        for (int v = 0; v < M; ++v)
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            if (PDE::flux_nonzero(d, v)) g[v] += part[d][v];
       }
     }
     __syncthreads();
@@ -390,12 +413,11 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       dk[v] = uu[v];
       qb[v] = uu[v];
     }
-    Real c = Real(1);
 #pragma unroll
     for (int k = 1; k <= N; ++k) {
       Real g[M];
       divergence(dk, g);
-      c = c * Real(dt) / Real(k + 1);
+      const Real c = sCk[k];
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         dk[v] = -g[v];
