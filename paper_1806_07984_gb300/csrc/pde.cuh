@@ -18,7 +18,6 @@ struct Euler {
 
   // Whether component v of f_d can be nonzero (Euler: every component).
   __host__ __device__ static constexpr bool flux_nonzero(int, int) { return true; }
-  static constexpr bool kSparseFlux = false;
 
   // All DIM fluxes at one node.
   template <class R>
@@ -86,7 +85,6 @@ struct Acoustics {
   // f_d has two nonzero components, p-row (v_d) and v_d-row (p); the kernels
   // skip the contractions of the others (adding their zeros changes nothing).
   __host__ __device__ static constexpr bool flux_nonzero(int d, int v) { return v == 0 || v == 1 + d; }
-  static constexpr bool kSparseFlux = true;
 
   template <class R>
   __device__ __forceinline__ static void fluxes(const R (&q)[M], R (&f)[DIM][M], R) {

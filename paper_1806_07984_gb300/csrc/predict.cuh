@@ -348,18 +348,12 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
       for (int v = 0; v < M; ++v) g[v] = settle(g[v]);
     } else {
-      // Sparse fluxes (few nonzero components per direction) leave few
-      // independent sums per node; there each (d, v) gets its own partial
-      // sum, added over d at the end, which shortens the dependent FMA chains.
-      Real part[DIM][M];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int base = node - id[d] * stride[d];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
           if (!PDE::flux_nonzero(d, v)) continue;
-          Real& acc = PDE::kSparseFlux ? part[d][v] : g[v];
-          if (PDE::kSparseFlux) acc = Real(0);
           const Real* line = my_fb + (d * M + v) * NS + base;
           if constexpr (kDinRegs && n % 2 == 0) {
             // FP32 x-lines are contiguous and 8-byte aligned (they start at a
@@ -369,8 +363,8 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 #pragma unroll
               for (int j2 = 0; j2 < n / 2; ++j2) {
                 const float2 p = l2[j2];
-                acc = fma(Dr[0][2 * j2], p.x, acc);
-                acc = fma(Dr[0][2 * j2 + 1], p.y, acc);
+                g[v] = fma(Dr[0][2 * j2], p.x, g[v]);
+                g[v] = fma(Dr[0][2 * j2 + 1], p.y, g[v]);
               }
               continue;
             }
@@ -387,16 +381,9 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
               jj = j + rz;
               jj = jj >= n ? jj - n : jj;
             }
-            acc = fma(dj, line[jj * stride[d]], acc);
+            g[v] = fma(dj, line[jj * stride[d]], g[v]);
           }
         }
-      }
-      if constexpr (PDE::kSparseFlux) {
-#pragma unroll
-        for (int v = 0; v < M; ++v)
-#pragma unroll
-          for (int d = 0; d < DIM; ++d)
-            if (PDE::flux_nonzero(d, v)) g[v] += part[d][v];
       }
     }
     __syncthreads();
