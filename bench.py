@@ -478,34 +478,49 @@ def run_ck(torch, order=4, base=54, steps=5, warmup=3):
     return out
 
 
+def indicator_flops_per_cell(dim, order, deriv):
+    """Algorithmic flops of the refinement indicator per cell (FMA = 2):
+    per node dim first derivatives (2n + 1 each); then either their squares
+    (2 each) or the dim (dim + 1) / 2 distinct Hessian entries (2n + 1 each)
+    and their weighted squares (2 each)."""
+    n = order + 1
+    per_node = dim * (2 * n + 1)
+    per_node += 2 * dim if deriv == 1 else dim * (dim + 1) // 2 * (2 * n + 3)
+    return n ** dim * per_node
+
+
 def run_indicator(s, torch, reps=5):
-    """The solution-based refinement indicator (ader_gradient_indicator, one
-    variable) on the bench mesh: device time per launch (CUDA events) against
-    the FP64 ALU peak, and the host-synchronous ader_gradient_flags call."""
+    """The solution-based refinement indicator (ader_gradient_indicator on the
+    density, first derivatives and Hessian) on the bench mesh: device time per
+    launch (CUDA events) against the FP64 ALU peak, and the host-synchronous
+    ader_gradient_flags call."""
     from paper_1806_07984_gb300 import ader as A
     st = torch.cuda.current_stream()
     eta = torch.empty(s.ncells, dtype=torch.float64, device=s.device)
-    A.ader_gradient_indicator(s.ctx, 0, eta, st.cuda_stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(reps):
-        A.ader_gradient_indicator(s.ctx, 0, eta, st.cuda_stream)
-    e1.record(st)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / reps
-    n, NS = s.n, s.n ** s.dim
-    fl = s.ncells * NS * s.dim * (2 * n + 3)
-    by = s.ncells * (NS + 1) * 8
-    c0 = time.perf_counter()
-    s.gradient_flags(0, 1.0, 0.1)
-    t_flags = time.perf_counter() - c0
-    return {"launch_ms": t * 1e3, "cells_per_s": s.ncells / t,
+    out = {}
+    for deriv in (1, 2):
+        A.ader_gradient_indicator(s.ctx, 0, eta, st.cuda_stream, deriv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            A.ader_gradient_indicator(s.ctx, 0, eta, st.cuda_stream, deriv)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        fl = s.ncells * indicator_flops_per_cell(s.dim, s.order, deriv)
+        by = s.ncells * (s.n ** s.dim + 1) * 8
+        c0 = time.perf_counter()
+        s.gradient_flags(0, 1.0, 0.1, deriv)
+        t_flags = time.perf_counter() - c0
+        out[f"deriv{deriv}"] = {
+            "launch_ms": t * 1e3, "cells_per_s": s.ncells / t,
             "roofline": {"bound": "alu", "achieved": fl / t / 1e12, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": fl / t / 1e12 / FP64_PEAK_TFLOPS,
                          "algorithmic_flops": fl, "algorithmic_bytes": by, "hbm_gbs": by / t / 1e9},
-            "gradient_flags_call_ms": t_flags * 1e3,
-            "workload": "density derivative on the bench mesh (%d cells)" % s.ncells}
+            "gradient_flags_call_ms": t_flags * 1e3}
+    out["workload"] = "density derivatives on the bench mesh (%d cells)" % s.ncells
+    return out
 
 
 def time_predictor(s, torch, reps=3):

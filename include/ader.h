@@ -230,23 +230,28 @@ ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
  * into children, L2 projection onto parents).  Synchronises the device. */
 ader_status ader_remesh(ader_ctx* ctx, const int8_t* flags);
 
-/* Solution-based criterion (Sec. 2.4: first derivatives of the solution),
- * the AMR epilogue of the corrector: eta[c] = max over the nodes of
- * h_c |grad u_var| with h_c = max_d h_d, computed on the device from the
- * current state; flags[c] = +1 if eta > refine_above and the cell is below
- * max_level, -1 if eta < coarsen_below and the cell is above level 0, else 0.
- * eta_out (host, may be NULL) and flags (host) have one entry per cell in mesh
- * order.  Synchronises the device before and after. */
-ader_status ader_gradient_flags(ader_ctx* ctx, int var, double refine_above, double coarsen_below,
-                                double* eta_out, int8_t* flags);
+/* Solution-based criterion (Sec. 2.4: first or second derivatives of the
+ * solution), the AMR epilogue of the corrector, computed on the device from
+ * the current state, with h_c = max_d h_d:
+ *   deriv 1: eta[c] = max over the nodes of h_c |grad u_var|,
+ *   deriv 2: eta[c] = max over the nodes of h_c^2 |Hessian of u_var|_F
+ * (Frobenius norm, mixed entries included); flags[c] = +1 if eta > refine_above
+ * and the cell is below max_level, -1 if eta < coarsen_below and the cell is
+ * above level 0, else 0.  eta_out (host, may be NULL) and flags (host) have
+ * one entry per cell in mesh order.  Synchronises the device before and after.
+ * ADER_ERR_ARG for var outside [0, nvar), deriv other than 1 or 2, or
+ * refine_above < coarsen_below. */
+ader_status ader_gradient_flags(ader_ctx* ctx, int var, int deriv, double refine_above,
+                                double coarsen_below, double* eta_out, int8_t* flags);
 
 /* The indicator eta of ader_gradient_flags alone, on the device: eta_dev
  * (device, caller-owned, ncells doubles, mesh order) receives eta[c] for
- * variable var (0 <= var < nvar) from the current state, asynchronously on
- * `stream` (a cudaStream_t; NULL = the legacy default stream).  The caller
- * orders it after the step that wrote the state (same stream, or an event).
- * ADER_ERR_ARG for a bad var or a NULL eta_dev with cells present. */
-ader_status ader_gradient_indicator(ader_ctx* ctx, int var, double* eta_dev, void* stream);
+ * variable var and derivative order deriv (1 or 2) from the current state,
+ * asynchronously on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  The caller orders it after the step that wrote the state (same
+ * stream, or an event).  ADER_ERR_ARG for a bad var or deriv, or a NULL
+ * eta_dev with cells present. */
+ader_status ader_gradient_indicator(ader_ctx* ctx, int var, int deriv, double* eta_dev, void* stream);
 
 /* Skeleton batch: transition cells plus cells with flags[c] > 0 (flags may be
  * NULL).  Host call; uploads the new lists (synchronous). */

@@ -131,9 +131,9 @@ def lib():
         "ader_batch_status_word": ([_vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "ader_batch_launch_count": ([_vp, _i64p], ctypes.c_int),
         "ader_adjoint_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
-        "ader_gradient_flags": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp],
-                                ctypes.c_int),
-        "ader_gradient_indicator": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_gradient_flags": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 _vp, _vp], ctypes.c_int),
+        "ader_gradient_indicator": ([_vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
         "ader_sample": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
         "ader_sample_adjoint": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
                                 ctypes.c_int),
@@ -459,19 +459,20 @@ def ader_sample_adjoint(ctx, npts, cells_dev, weights_dev, var, values_dev, fiel
            "ader_sample_adjoint")
 
 
-def ader_gradient_flags(ctx, var, refine_above, coarsen_below):
+def ader_gradient_flags(ctx, var, refine_above, coarsen_below, deriv=1):
     ncells = ader_mesh_info(ctx)[0]
     eta = np.zeros(ncells, dtype=np.float64)
     flags = np.zeros(ncells, dtype=np.int8)
-    _check(ctx, lib().ader_gradient_flags(ctx, var, float(refine_above), float(coarsen_below),
-                                          _ptr(eta), _ptr(flags)), "ader_gradient_flags")
+    _check(ctx, lib().ader_gradient_flags(ctx, var, int(deriv), float(refine_above),
+                                          float(coarsen_below), _ptr(eta), _ptr(flags)),
+           "ader_gradient_flags")
     return eta, flags
 
 
-def ader_gradient_indicator(ctx, var, eta_dev, stream=None):
+def ader_gradient_indicator(ctx, var, eta_dev, stream=None, deriv=1):
     """eta (device array of ncells doubles) of ader_gradient_flags, enqueued on
     ``stream`` (a raw cudaStream_t handle; None = legacy default stream)."""
-    _check(ctx, lib().ader_gradient_indicator(ctx, var, _ptr(eta_dev), stream),
+    _check(ctx, lib().ader_gradient_indicator(ctx, var, int(deriv), _ptr(eta_dev), stream),
            "ader_gradient_indicator")
 
 

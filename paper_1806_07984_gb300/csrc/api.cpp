@@ -870,12 +870,13 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
 
 namespace {
 
-cudaError_t enqueue_indicator(ader_ctx* c, int var, double* eta, cudaStream_t s) {
+cudaError_t enqueue_indicator(ader_ctx* c, int var, int deriv, double* eta, cudaStream_t s) {
   IndicatorArgs a{};
   a.u = c->u;
   a.level = c->level;
   a.ncells = int64_t(c->tree.cells.size());
   a.var = var;
+  a.deriv = deriv;
   a.eta = eta;
   std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
   a.B = c->B;
@@ -888,22 +889,24 @@ cudaError_t enqueue_indicator(ader_ctx* c, int var, double* eta, cudaStream_t s)
 
 }  // namespace
 
-ader_status ader_gradient_indicator(ader_ctx* c, int var, double* eta_dev, void* stream) {
-  if (!c || var < 0 || var >= c->M) return ADER_ERR_ARG;
+ader_status ader_gradient_indicator(ader_ctx* c, int var, int deriv, double* eta_dev, void* stream) {
+  if (!c || var < 0 || var >= c->M || (deriv != 1 && deriv != 2)) return ADER_ERR_ARG;
   if (!eta_dev && !c->tree.cells.empty()) return ADER_ERR_ARG;
-  CK(enqueue_indicator(c, var, eta_dev, static_cast<cudaStream_t>(stream)), "gradient indicator");
+  CK(enqueue_indicator(c, var, deriv, eta_dev, static_cast<cudaStream_t>(stream)), "gradient indicator");
   return ADER_OK;
 }
 
-ader_status ader_gradient_flags(ader_ctx* c, int var, double refine_above, double coarsen_below,
+ader_status ader_gradient_flags(ader_ctx* c, int var, int deriv, double refine_above, double coarsen_below,
                                 double* eta_out, int8_t* flags) {
-  if (!c || !flags || var < 0 || var >= c->M || !(refine_above >= coarsen_below)) return ADER_ERR_ARG;
+  if (!c || !flags || var < 0 || var >= c->M || (deriv != 1 && deriv != 2) ||
+      !(refine_above >= coarsen_below))
+    return ADER_ERR_ARG;
   const int64_t C = int64_t(c->tree.cells.size());
   // the state may still be written by steps on the caller's (non-blocking) streams
   CK(cudaDeviceSynchronize(), "sync before gradient indicator");
   double* d_eta = nullptr;
   CK(cudaMalloc(&d_eta, sizeof(double) * size_t(std::max<int64_t>(C, 1))), "cudaMalloc eta");
-  cudaError_t e = enqueue_indicator(c, var, d_eta, nullptr);
+  cudaError_t e = enqueue_indicator(c, var, deriv, d_eta, nullptr);
   std::vector<double> eta(static_cast<size_t>(C));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess && C > 0)

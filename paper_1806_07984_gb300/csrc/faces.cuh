@@ -468,19 +468,24 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::NS) transfer_kernel(cons
   for (int v = 0; v < M; ++v) a.u_new[(c * M + v) * NS + node] = acc[v];
 }
 
-// Refinement indicator (epilogue of the corrector): per cell the largest
-// h |grad q| over its nodes, for one variable q.  The nodes reduce |grad q|^2
-// (a tree maximum over the FP64 bit patterns, which order like the values for
-// non-negative doubles); the square root and h follow once per cell, which
-// gives the same value as taking them per node (both are monotone and
-// correctly rounded).
-template <int DIM, int N, int M>
+// Refinement indicator (epilogue of the corrector), for one variable q:
+// DERIV 1, per cell the largest h |grad q| over its nodes; DERIV 2, the
+// largest h^2 |H q|_F with H the Hessian (the mixed entries from the first
+// derivatives, kept in shared memory, differentiated along the other axis;
+// each pair a < b counted twice).  The nodes reduce the squared norm (a tree
+// maximum over the FP64 bit patterns, which order like the values for
+// non-negative doubles); the square root and the power of h follow once per
+// cell, which gives the same value as taking them per node (both are
+// monotone and correctly rounded).
+template <int DIM, int N, int M, int DERIV>
 __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kernel(const IndicatorArgs a) {
   using SH = PredictShape<DIM, N>;
   constexpr int n = SH::n, NS = SH::NS, CPB = SH::CPB;
   constexpr int kPow2 = pow2_ceil(NS);
+  constexpr int NG = DERIV == 2 ? DIM : 1;
   __shared__ double q[CPB][NS];
   __shared__ double sD[n * n];
+  __shared__ double gsh[CPB][NG][NS];
   __shared__ unsigned long long r[CPB][NS];
   const int tid = threadIdx.x;
   const int cl = tid / NS;
@@ -501,7 +506,24 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kerne
 #pragma unroll
     for (int j = 0; j < n; ++j) s = fma(sD[id[d] * n + j], q[cl][base + j * stride[d]], s);
     s *= a.inv_h[lv][d];
-    g2 = fma(s, s, g2);
+    if constexpr (DERIV == 2)
+      gsh[cl][d][node] = s;
+    else
+      g2 = fma(s, s, g2);
+  }
+  if constexpr (DERIV == 2) {
+    __syncthreads();
+#pragma unroll
+    for (int da = 0; da < DIM; ++da)
+#pragma unroll
+      for (int db = da; db < DIM; ++db) {
+        const int base = node - id[db] * stride[db];
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) s = fma(sD[id[db] * n + j], gsh[cl][da][base + j * stride[db]], s);
+        s *= a.inv_h[lv][db];
+        g2 = fma(da == db ? s : 2.0 * s, s, g2);
+      }
   }
   r[cl][node] = static_cast<unsigned long long>(__double_as_longlong(g2));
   for (int st = kPow2 / 2; st > 0; st >>= 1) {
@@ -512,7 +534,8 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) indicator_kerne
     double hmax = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) hmax = fmax(hmax, 1.0 / a.inv_h[lv][d]);
-    a.eta[cell] = sqrt(__longlong_as_double(static_cast<long long>(r[cl][0]))) * hmax;
+    const double w = DERIV == 2 ? hmax * hmax : hmax;
+    a.eta[cell] = sqrt(__longlong_as_double(static_cast<long long>(r[cl][0]))) * w;
   }
 }
 
@@ -520,7 +543,11 @@ template <int DIM, int N, int M>
 cudaError_t launch_indicator_t(const IndicatorArgs& a, cudaStream_t s) {
   using SH = PredictShape<DIM, N>;
   if (a.ncells == 0) return cudaSuccess;
-  indicator_kernel<DIM, N, M><<<unsigned((a.ncells + SH::CPB - 1) / SH::CPB), SH::THREADS, 0, s>>>(a);
+  const unsigned blocks = unsigned((a.ncells + SH::CPB - 1) / SH::CPB);
+  if (a.deriv == 2)
+    indicator_kernel<DIM, N, M, 2><<<blocks, SH::THREADS, 0, s>>>(a);
+  else
+    indicator_kernel<DIM, N, M, 1><<<blocks, SH::THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 

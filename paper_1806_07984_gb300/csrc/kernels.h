@@ -81,13 +81,16 @@ struct CorrectArgs {
   BasisTables B;
 };
 
-// Solution-based refinement indicator: eta[c] = max over the nodes of h_c
-// |grad u_var| with h_c = max_d h_d (first derivatives by D along each axis).
+// Solution-based refinement indicator, h_c = max_d h_d:
+//   deriv 1: eta[c] = max over the nodes of h_c |grad u_var|;
+//   deriv 2: eta[c] = max over the nodes of h_c^2 |Hessian of u_var|_F
+// (derivatives by D along each axis).
 struct IndicatorArgs {
   const double* u;
   const int8_t* level;
   int64_t ncells;
   int var;
+  int deriv;  // 1 or 2
   double* eta;
   double inv_h[kMaxLevels][3];
   BasisTables B;

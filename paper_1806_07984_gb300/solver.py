@@ -142,13 +142,15 @@ class Solver:
     def classify(self, flags=None):
         A.ader_classify(self.ctx, flags)
 
-    def gradient_flags(self, var, refine_above, coarsen_below):
-        return A.ader_gradient_flags(self.ctx, var, refine_above, coarsen_below)
+    def gradient_flags(self, var, refine_above, coarsen_below, deriv=1):
+        """(eta, flags): eta = h |grad q| (deriv 1) or h^2 |Hessian q|_F
+        (deriv 2) per cell, q = variable ``var``."""
+        return A.ader_gradient_flags(self.ctx, var, refine_above, coarsen_below, deriv)
 
-    def gradient_indicator(self, var, stream=None):
+    def gradient_indicator(self, var, stream=None, deriv=1):
         """Device tensor eta[c] of gradient_flags, enqueued on ``stream``."""
         eta = self.torch.empty(self.ncells, dtype=self.torch.float64, device=self.device)
-        A.ader_gradient_indicator(self.ctx, var, eta, self._stream(stream))
+        A.ader_gradient_indicator(self.ctx, var, eta, self._stream(stream), deriv)
         return eta
 
     def sphere_flags(self, center, radius):

@@ -222,13 +222,14 @@ def test_solution_based_remesh_parity():
     assert solver.status() == 0
 
 
+@pytest.mark.parametrize("deriv", [1, 2])
 @pytest.mark.parametrize("dim,order,pde,var", [(2, 3, "euler", 0), (2, 7, "euler", 3),
                                                (3, 2, "euler", 4), (3, 5, "euler", 1),
                                                (3, 7, "acoustics", 0), (2, 4, "acoustics", 2)])
-def test_gradient_indicator_parity(dim, order, pde, var):
-    """The asynchronous device indicator on an AMR mesh (a ragged last block
-    of cells in 2D) equals the oracle's eta to 1e-12 and the eta returned by
-    gradient_flags bit for bit."""
+def test_gradient_indicator_parity(dim, order, pde, var, deriv):
+    """The asynchronous device indicator (first derivatives, or the Hessian)
+    on an AMR mesh (a ragged last block of cells in 2D) equals the oracle's
+    eta to 1e-12 and the eta returned by gradient_flags bit for bit."""
     from oracle import criterion
     import torch
     base, lvl = (7, 2) if dim == 2 else (3, 1)
@@ -241,15 +242,20 @@ def test_gradient_indicator_parity(dim, order, pde, var):
         u = workloads.random_acoustics(rng, dim, (len(om.cells),) + (B.n,) * dim)
     u = np.ascontiguousarray(np.moveaxis(u, 0, 1))
     solver.set_state(u[perm])
-    eta_o, _ = criterion.gradient_flags(om, u, B, var, 1.0, 0.5)
+    eta_o, fl_o = criterion.gradient_flags(om, u, B, var, 1.0, 0.5, deriv=deriv)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        eta_a = solver.gradient_indicator(var, stream=st)
+        eta_a = solver.gradient_indicator(var, stream=st, deriv=deriv)
     st.synchronize()
     eta_a = eta_a.cpu().numpy()
     assert rel_l2(eta_a, eta_o[perm]) < 1e-12
-    eta_g, _ = solver.gradient_flags(var, 1.0, 0.5)
+    eta_g, fl_g = solver.gradient_flags(var, 1.0, 0.5, deriv=deriv)
     assert np.array_equal(eta_a, eta_g)
+    near = (np.abs(eta_o[perm] - 1.0) < 1e-10) | (np.abs(eta_o[perm] - 0.5) < 1e-10)
+    assert np.array_equal(fl_g[~near], fl_o[perm][~near])
+    from paper_1806_07984_gb300 import ader as A
+    with pytest.raises(A.AderError):
+        solver.gradient_flags(var, 1.0, 0.5, deriv=3)
 
 
 # Double-float predictor (pairs of FP32 values, ~48 significant bits): stated

@@ -186,3 +186,38 @@ def test_gradient_indicator_of_linear_and_quadratic_fields():
     _, fl = criterion.gradient_flags(m, u, B, 0, 5.0 / 4, 5.0 / 10)
     assert fl.tolist() == [1 if 5.0 * hh > 5.0 / 4 else (-1 if k[0] > 0 and 5.0 * hh < 0.5 else 0)
                            for hh, k in zip(h[:, 0], m.cells)]
+
+
+def test_hessian_indicator_closed_forms():
+    """eta = h^2 |H q|_F against closed forms on an anisotropic 2-level mesh
+    (h_x != h_y, so a derivative taken along the wrong axis or divided by the
+    wrong width fails): linear -> 0, y^2 -> 2 h^2, x y -> sqrt(2) h^2 (the mixed
+    entries count), x^3 -> 6 max|x| h^2 (exact at N = 3), and in 3D
+    x^2 + y^2 + z^2 -> 2 sqrt(3) h^2."""
+    from oracle import criterion
+    N = 3
+    B = basis.Basis(N)
+    m = meshmod.Mesh(2, (3, 9), 1)
+    m.remesh(np.zeros((len(m.cells), 1) + (2, 2)), np.array([1] + [0] * (len(m.cells) - 1), dtype=np.int8),
+             basis.Basis(1))
+    X = m.node_coords(B.xi)
+    h = m.cell_widths()
+    assert not np.allclose(h[:, 0], h[:, 1])
+    hm = h.max(axis=1)
+    fields = [2.0 * X[0] - 5.0 * X[1] + 1.0, X[1] ** 2, X[0] * X[1], X[0] ** 3]
+    u = np.stack(fields, axis=1)
+    eta = [criterion.gradient_indicator(u, h, B, v, deriv=2) for v in range(4)]
+    assert np.all(np.abs(eta[0]) < 1e-9 * hm ** 2 / h.min(axis=1) ** 2)
+    assert np.allclose(eta[1], 2.0 * hm ** 2, rtol=1e-11)
+    assert np.allclose(eta[2], np.sqrt(2.0) * hm ** 2, rtol=1e-11)
+    xmax = np.abs(X[0].reshape(len(m.cells), -1)).max(axis=1)
+    assert np.allclose(eta[3], 6.0 * xmax * hm ** 2, rtol=1e-11)
+    m3 = meshmod.Mesh(3, (3, 3, 3), 0)
+    X3 = m3.node_coords(B.xi)
+    h3 = m3.cell_widths()
+    u3 = np.stack([X3[0] ** 2 + X3[1] ** 2 + X3[2] ** 2], axis=1)
+    eta3 = criterion.gradient_indicator(u3, h3, B, 0, deriv=2)
+    assert np.allclose(eta3, 2.0 * np.sqrt(3.0) * h3.max(axis=1) ** 2, rtol=1e-11)
+    thr = 2.0 / 81.0 * 1.0001      # between the fine cells' 2 (1/9)^2 and the coarse ones' 2 (1/3)^2
+    _, fl = criterion.gradient_flags(m, u, B, 1, thr, thr, deriv=2)
+    assert fl.tolist() == [1 if k[0] == 0 else -1 for k in m.cells]
