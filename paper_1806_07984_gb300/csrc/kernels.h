@@ -7,6 +7,7 @@
 //   faceQ, faceF  [c][2 * dir + side][var][fnode]   (side 0: xi_dir = 0)
 //   fstar         [c][2 * dir + side][var][fnode]
 #pragma once
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -145,6 +146,21 @@ cudaError_t launch_limiter_2d(int order, int pde, LimiterKernel which, const Lim
 cudaError_t launch_limiter_3d(int order, int pde, LimiterKernel which, const LimiterArgs& a, int grid,
                               cudaStream_t s);
 int64_t limiter_fv_scratch_3d(int order, int pde);
+
+// Opt `kernel` into `bytes` of dynamic shared memory on the current device.
+// The attribute is per device, so it is set once per device; `done` is the
+// caller's per-kernel set of devices already configured (one bit each).
+template <class K>
+inline cudaError_t smem_opt_in(std::atomic<uint64_t>& done, K kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit != 0 && (done.load(std::memory_order_acquire) & bit) != 0) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 enum class Precision { kFP64 = 0, kFP32 = 1, kTF32 = 2, kTF32x3 = 3, kBF16x3 = 4, kDF64 = 5 };
 

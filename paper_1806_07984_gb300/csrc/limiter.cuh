@@ -561,14 +561,11 @@ cudaError_t launch_limiter_t(LimiterKernel which, const LimiterArgs& a, int grid
     if (a.ncells == 0) return cudaSuccess;
     const size_t bytes = sizeof(double) * size_t(S * n + 16 * M + M * L::NS +
                                                  M * partial_scratch<DIM, N>());
-    static bool configured = false;  // per process: set once, outside any graph capture
-    if (!configured) {
-      cudaFuncSetAttribute(limiter_bounds_kernel<DIM, N, PDE>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      cudaFuncSetAttribute(limiter_detect_kernel<DIM, N, PDE>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      configured = true;
-    }
+    static std::atomic<uint64_t> bounds_set{0}, detect_set{0};
+    cudaError_t e = which == LimiterKernel::kBounds
+                        ? smem_opt_in(bounds_set, limiter_bounds_kernel<DIM, N, PDE>, bytes)
+                        : smem_opt_in(detect_set, limiter_detect_kernel<DIM, N, PDE>, bytes);
+    if (e != cudaSuccess) return e;
     if (which == LimiterKernel::kBounds)
       limiter_bounds_kernel<DIM, N, PDE><<<unsigned(a.ncells), L::CELL_THREADS, bytes, s>>>(a);
     else
@@ -576,12 +573,9 @@ cudaError_t launch_limiter_t(LimiterKernel which, const LimiterArgs& a, int grid
   } else if (which == LimiterKernel::kFV) {
     const size_t bytes = sizeof(double) * size_t(FvSmem<DIM, N, M>::smem);
     if (FvSmem<DIM, N, M>::kBig && !a.fv_scratch) return cudaErrorInvalidValue;
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(limiter_fv_kernel<DIM, N, PDE>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-      configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    cudaError_t e = smem_opt_in(configured, limiter_fv_kernel<DIM, N, PDE>, bytes);
+    if (e != cudaSuccess) return e;
     limiter_fv_kernel<DIM, N, PDE><<<unsigned(grid), L::THREADS, bytes, s>>>(a);
   } else {
     limiter_fix_kernel<DIM, N, PDE><<<unsigned(grid), 128, 0, s>>>(a);

@@ -638,13 +638,9 @@ cudaError_t launch_predict_tc_t(const PredictArgs& a, cudaStream_t s) {
   using L = TcLayout<3, N, PDE, TC>;
   if (a.count == 0) return cudaSuccess;
   const size_t smem = PredictSmem<3, N, PDE, float>::bytes() + L::bytes();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(predict_tc_kernel<N, PDE, TC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t e = smem_opt_in(configured, predict_tc_kernel<N, PDE, TC>, smem);
+  if (e != cudaSuccess) return e;
   predict_tc_kernel<N, PDE, TC><<<dim3(unsigned(a.count)), dim3(L::THREADS), smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -654,13 +650,9 @@ cudaError_t launch_predict_t(const PredictArgs& a, cudaStream_t s) {
   using S = PredictShape<DIM, N>;
   if (a.count == 0) return cudaSuccess;
   const size_t smem = PredictSmem<DIM, N, PDE, Real>::bytes();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(predict_kernel<DIM, N, PDE, Real, SCHEME>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t e = smem_opt_in(configured, predict_kernel<DIM, N, PDE, Real, SCHEME>, smem);
+  if (e != cudaSuccess) return e;
   const int64_t blocks = (a.count + S::CPB - 1) / S::CPB;
   predict_kernel<DIM, N, PDE, Real, SCHEME><<<dim3(unsigned(blocks)), dim3(S::THREADS), smem, s>>>(a);
   return cudaGetLastError();
