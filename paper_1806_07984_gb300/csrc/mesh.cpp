@@ -4,10 +4,32 @@
 #include "mesh.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <thread>
 
 namespace ader {
+
+namespace {
+
+// Threads for a host pass over n items: one per 4096 items, at most 16 and
+// the hardware's count.
+int pass_threads(int64_t n) {
+  const int64_t hw = int64_t(std::max(1u, std::thread::hardware_concurrency()));
+  return int(std::max<int64_t>(1, std::min<int64_t>(hw, std::min<int64_t>(16, n / 4096))));
+}
+
+// f(t, begin, end) on the T contiguous ranges [n t / T, n (t + 1) / T) of
+// [0, n), range 0 on the calling thread.
+template <class F>
+void parallel_ranges(int64_t n, int T, F&& f) {
+  std::vector<std::thread> workers;
+  for (int t = 1; t < T; ++t) workers.emplace_back([&, t] { f(t, n * t / T, n * (t + 1) / T); });
+  f(0, int64_t(0), n / T);
+  for (std::thread& w : workers) w.join();
+}
+
+}  // namespace
 
 uint64_t pack(const Key& k) {
   return (uint64_t(k.level) << 60) | (uint64_t(k.x[0] & 0xFFFFF) << 40) |
@@ -108,20 +130,10 @@ void Tree::split(const Key& k) {
       }
 }
 
-void Tree::rebuild_refined() {
-  refined_.reset(leaves_.size() / 2 + 16);
-  leaves_.for_each([&](uint64_t v, int32_t) {
-    Key k = unpack(v);
-    while (k.level > 0) {
-      k = parent(k);
-      if (!refined_.insert(pack(k))) break;
-    }
-  });
-}
-
-void Tree::dfs(const Key& k, std::vector<Key>* out) const {
-  if (is_leaf(k)) {
+void Tree::dfs(const Key& k, std::vector<Key>* out, std::vector<int32_t*>* slots) {
+  if (int32_t* pos = leaves_.find_mut(pack(k))) {
     out->push_back(k);
+    slots->push_back(pos);
     return;
   }
   if (!is_refined(k)) return;
@@ -130,23 +142,44 @@ void Tree::dfs(const Key& k, std::vector<Key>* out) const {
     for (int sy = 0; sy < 3; ++sy)
       for (int sx = 0; sx < 3; ++sx) {
         int s[3] = {sx, sy, sz};
-        dfs(child(k, s), out);
+        dfs(child(k, s), out, slots);
       }
 }
 
-void Tree::order_cells(std::vector<Key>* out) const {
-  out->clear();
-  out->reserve(leaves_.size());
-  for (int z = 0; z < base_[2]; ++z)
-    for (int y = 0; y < base_[1]; ++y)
-      for (int x = 0; x < base_[0]; ++x) dfs(Key{0, {x, y, z}}, out);
+void Tree::order_cells(std::vector<Key>* out) {
+  // base cells x fastest, each followed by its subtree.  The refined region
+  // is local, so the base cells go in many small contiguous groups, taken by
+  // the threads in turn and concatenated in group order.
+  const int64_t nb = int64_t(base_[0]) * base_[1] * base_[2];
+  const int T = pass_threads(int64_t(leaves_.size()));
+  const int64_t G = std::min<int64_t>(nb, int64_t(T) * 64);
+  std::vector<std::vector<Key>> part(static_cast<size_t>(G));
+  std::vector<std::vector<int32_t*>> slot(static_cast<size_t>(G));
+  std::atomic<int64_t> next{0};
+  auto work = [&]() {
+    for (int64_t g = next++; g < G; g = next++)
+      for (int64_t i = nb * g / G; i < nb * (g + 1) / G; ++i) {
+        const Key k{0, {int(i % base_[0]), int((i / base_[0]) % base_[1]),
+                        int(i / (int64_t(base_[0]) * base_[1]))}};
+        dfs(k, &part[size_t(g)], &slot[size_t(g)]);
+      }
+  };
+  parallel_ranges(T, T, [&](int, int64_t, int64_t) { work(); });
+  std::vector<size_t> off(static_cast<size_t>(G) + 1, 0);
+  for (int64_t g = 0; g < G; ++g) off[size_t(g) + 1] = off[size_t(g)] + part[size_t(g)].size();
+  out->resize(off[size_t(G)]);
+  parallel_ranges(G, T, [&](int, int64_t b, int64_t e) {
+    for (int64_t g = b; g < e; ++g)
+      for (size_t i = 0; i < part[size_t(g)].size(); ++i) {
+        (*out)[off[size_t(g)] + i] = part[size_t(g)][i];
+        *slot[size_t(g)][i] = int32_t(off[size_t(g)] + i);
+      }
+  });
 }
 
 bool Tree::build() {
-  order_cells(&cells);
+  order_cells(&cells);  // also sets every leaf's position in leaves_
   const int64_t n = int64_t(cells.size());
-  KeyMap pos(static_cast<size_t>(n));
-  for (int64_t i = 0; i < n; ++i) pos.insert(pack(cells[size_t(i)]), int32_t(i));
   conf_all.clear();
   parents.clear();
   child_fine.clear();
@@ -160,25 +193,37 @@ bool Tree::build() {
     std::vector<int32_t> child_fine, marked;
     bool ok = true;
   };
-  const int nt = int(std::max<int64_t>(1, std::min<int64_t>(
-      int64_t(std::max(1u, std::thread::hardware_concurrency())), std::min<int64_t>(16, n / 4096))));
+  const int nt = pass_threads(n);
   std::vector<Part> parts(static_cast<size_t>(nt));
-  auto sweep = [&](int t) {
+  parallel_ranges(n, nt, [&](int t, int64_t b, int64_t e) {
     Part& P = parts[size_t(t)];
+    P.conf.reserve(size_t(e - b) * size_t(dim_));
     std::vector<Key> kids;
-    const int64_t b = n * t / nt, e = n * (t + 1) / nt;
     for (int64_t i = b; i < e && P.ok; ++i) {
       const Key k = cells[size_t(i)];
       for (int dir = 0; dir < dim_; ++dir) {
         for (int side = 1; side >= 0; --side) {
           Key nb = neighbor(k, dir, side);
-          if (side == 1 && is_leaf(nb)) {
-            P.conf.push_back({int32_t(i), *pos.find(pack(nb)), dir, 0});
+          const uint64_t key = pack(nb);
+          // A leaf neighbour of the same level is usually a fixed distance
+          // away in the depth-first order (a sibling, or the next base cell):
+          // a key compare there saves the hash lookup.
+          const int64_t st = k.level > 0 ? (dir == 0 ? 1 : (dir == 1 ? 3 : 9))
+                                         : (dir == 0 ? 1 : (dir == 1 ? base_[0] : int64_t(base_[0]) * base_[1]));
+          const int64_t cand = side == 1 ? i + st : i - st;
+          int32_t at = -1;
+          if (cand >= 0 && cand < n && pack(cells[size_t(cand)]) == key) {
+            at = int32_t(cand);
+          } else if (const int32_t* leaf = leaves_.find(key)) {
+            at = *leaf;
+          }
+          if (at >= 0) {  // a leaf is never refined
+            if (side == 1) P.conf.push_back({int32_t(i), at, dir, 0});
           } else if (is_refined(nb)) {
             touching_children(nb, dir, 1 - side, &kids);
             P.parents.push_back({int32_t(i), dir, side, 0});
             for (const Key& c : kids) {
-              const int32_t* it = pos.find(pack(c));
+              const int32_t* it = leaves_.find(pack(c));
               if (!it) {
                 P.ok = false;
                 break;
@@ -191,11 +236,7 @@ bool Tree::build() {
         }
       }
     }
-  };
-  std::vector<std::thread> workers;
-  for (int t = 1; t < nt; ++t) workers.emplace_back(sweep, t);
-  sweep(0);
-  for (std::thread& w : workers) w.join();
+  });
   for (const Part& P : parts) {
     if (!P.ok) {
       error_ = "mesh is not 2:1 balanced";
@@ -220,18 +261,10 @@ void Tree::classify(const int8_t* refine_flags) {
     skeleton[i] = transition[i] || (refine_flags && refine_flags[i] > 0);
     (skeleton[i] ? skel_cells : encl_cells).push_back(int32_t(i));
   }
-  conf.clear();
-  conf.reserve(conf_all.size());
-  for (int pass = 0; pass < 2; ++pass)
-    for (const ConfFace& f : conf_all) {
-      const bool both = skeleton[size_t(f.left)] && skeleton[size_t(f.right)];
-      if (both == (pass == 0)) conf.push_back(f);
-    }
-  n_conf_skeleton = 0;
-  for (const ConfFace& f : conf_all)
-    n_conf_skeleton += (skeleton[size_t(f.left)] && skeleton[size_t(f.right)]) ? 1 : 0;
   // enclave pipeline: chunk of every cell (-1 = skeleton), faces by the later
-  // chunk of their two cells, cells by the latest chunk among their faces
+  // chunk of their two cells, cells by the latest chunk among their faces.
+  // conf = the faces with two skeleton cells (conf_all order), then the
+  // others grouped by that chunk (conf_all order within a group).
   const int K = std::max(1, chunks);
   const int64_t ne = int64_t(encl_cells.size());
   std::vector<int> chunk_of(n, -1);
@@ -240,22 +273,28 @@ void Tree::classify(const int8_t* refine_flags) {
   for (int k = 0; k < K; ++k)
     for (int64_t p = chunk_off[size_t(k)]; p < chunk_off[size_t(k) + 1]; ++p)
       chunk_of[size_t(encl_cells[size_t(p)])] = k;
-  std::vector<int> ready(n);
-  for (size_t i = 0; i < n; ++i) ready[i] = chunk_of[i];
-  std::vector<std::vector<ConfFace>> by_chunk(static_cast<size_t>(K));
-  for (size_t i = size_t(n_conf_skeleton); i < conf.size(); ++i) {
-    const ConfFace& f = conf[i];
-    const int r = std::max(chunk_of[size_t(f.left)], chunk_of[size_t(f.right)]);
-    by_chunk[size_t(r)].push_back(f);
-    ready[size_t(f.left)] = std::max(ready[size_t(f.left)], r);
-    ready[size_t(f.right)] = std::max(ready[size_t(f.right)], r);
+  std::vector<int> ready(chunk_of);
+  const size_t nf = conf_all.size();
+  std::vector<int> group(nf);  // -1: both cells skeleton, else the face's chunk
+  std::vector<int64_t> count(size_t(K) + 1, 0);
+  for (size_t f = 0; f < nf; ++f) {
+    const ConfFace& F = conf_all[f];
+    const int r = std::max(chunk_of[size_t(F.left)], chunk_of[size_t(F.right)]);
+    group[f] = r;
+    ++count[size_t(r + 1)];
+    if (r >= 0) {
+      ready[size_t(F.left)] = std::max(ready[size_t(F.left)], r);
+      ready[size_t(F.right)] = std::max(ready[size_t(F.right)], r);
+    }
   }
+  n_conf_skeleton = count[0];
   face_off.assign(size_t(K) + 1, 0);
-  size_t pos = size_t(n_conf_skeleton);
-  for (int k = 0; k < K; ++k) {
-    for (const ConfFace& f : by_chunk[size_t(k)]) conf[pos++] = f;
-    face_off[size_t(k) + 1] = int64_t(pos) - n_conf_skeleton;
-  }
+  for (int k = 0; k < K; ++k) face_off[size_t(k) + 1] = face_off[size_t(k)] + count[size_t(k) + 1];
+  std::vector<int64_t> put(size_t(K) + 1);
+  put[0] = 0;
+  for (int k = 0; k < K; ++k) put[size_t(k) + 1] = n_conf_skeleton + face_off[size_t(k)];
+  conf.resize(nf);
+  for (size_t f = 0; f < nf; ++f) conf[size_t(put[size_t(group[f] + 1)]++)] = conf_all[f];
   corr_off.assign(size_t(K) + 2, 0);
   for (size_t i = 0; i < n; ++i) ++corr_off[size_t(ready[i] + 1) + 1];
   for (int g = 0; g <= K; ++g) corr_off[size_t(g) + 1] += corr_off[size_t(g)];
@@ -296,8 +335,6 @@ void Tree::set_chunks(int K) {
 bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
                   std::vector<int32_t>* coarsen_children) {
   const std::vector<Key> old_cells = cells;
-  KeyMap old_index(old_cells.size());
-  for (size_t i = 0; i < old_cells.size(); ++i) old_index.insert(pack(old_cells[i]), int32_t(i));
   KeyMap coarsen;
   // 1. refine flagged leaves below max_level
   std::vector<Key> split_queue;
@@ -327,7 +364,6 @@ bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
           split_queue.push_back(cover);
         }
   }
-  rebuild_refined();
   // 3. coarsen complete families of flagged leaves whose parent stays balanced
   std::vector<uint64_t> fams;
   coarsen.for_each([&](uint64_t v, int32_t) {
@@ -361,10 +397,13 @@ bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
           leaves_.erase(pack(child(P, s)));
         }
     leaves_.insert(pack(P));
+    refined_.erase(pack(P));
   }
-  rebuild_refined();
   if (!build()) return false;
   // 4. transfer plan for the new order
+  if (plan_by_walk(old_cells, plan, coarsen_children)) return true;
+  KeyMap old_index(old_cells.size());
+  for (size_t i = 0; i < old_cells.size(); ++i) old_index.insert(pack(old_cells[i]), int32_t(i));
   plan->clear();
   coarsen_children->clear();
   for (const Key& k : cells) {
@@ -400,6 +439,53 @@ bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
   return true;
 }
 
+// Both cell lists are depth-first orders of the same base grid, and a remesh
+// changes cells by one level at most: the new list is the old one with every
+// refined leaf replaced in place by its 3^d children (lexicographic, x
+// fastest) and every coarsened family by its parent.  One merge walk over the
+// two lists therefore finds the source of every new cell; each entry is
+// checked against the keys, and the walk reports failure (the caller then
+// uses key lookups) on anything else.
+bool Tree::plan_by_walk(const std::vector<Key>& old_cells, std::vector<TransferItem>* plan,
+                        std::vector<int32_t>* coarsen_children) const {
+  plan->clear();
+  coarsen_children->clear();
+  plan->reserve(cells.size());
+  const int nz = dim_ == 3 ? 3 : 1;
+  const int fam = 9 * nz;
+  const size_t no = old_cells.size();
+  size_t j = 0;
+  for (const Key& k : cells) {
+    if (j >= no) return false;
+    const Key& o = old_cells[j];
+    TransferItem t{0, 0, 0, 0};
+    if (pack(k) == pack(o)) {
+      t.src = int32_t(j++);
+    } else if (k.level == o.level + 1 && pack(parent(k)) == pack(o)) {
+      t.kind = 1;
+      t.src = int32_t(j);
+      int s[3] = {0, 0, 0};
+      for (int d = 0; d < dim_; ++d) s[d] = k.x[d] - 3 * o.x[d];
+      t.child = s[0] + 3 * s[1] + 9 * s[2];
+      if (t.child == fam - 1) ++j;  // the parent's last child in the order
+    } else if (o.level == k.level + 1 && j + size_t(fam) <= no) {
+      t.kind = 2;
+      t.src = int32_t(coarsen_children->size());
+      for (int sz = 0; sz < nz; ++sz)
+        for (int sy = 0; sy < 3; ++sy)
+          for (int sx = 0; sx < 3; ++sx) {
+            int s[3] = {sx, sy, sz};
+            if (pack(old_cells[j]) != pack(child(k, s))) return false;
+            coarsen_children->push_back(int32_t(j++));
+          }
+    } else {
+      return false;
+    }
+    plan->push_back(t);
+  }
+  return j == no;
+}
+
 void Tree::sphere_flags(const double center[3], double radius, const double lo[3],
                         const double hi[3], int8_t* flags) const {
   auto meets = [&](const Key& k) {
@@ -420,15 +506,18 @@ void Tree::sphere_flags(const double center[3], double radius, const double lo[3
     }
     return dist2 <= radius * radius;
   };
-  for (size_t i = 0; i < cells.size(); ++i) {
-    const Key& k = cells[i];
-    int8_t f = 0;
-    if (k.level < max_level_ && meets(k))
-      f = 1;
-    else if (k.level > 0 && !meets(parent(k)))
-      f = -1;
-    flags[i] = f;
-  }
+  const int64_t n = int64_t(cells.size());
+  parallel_ranges(n, pass_threads(n), [&](int, int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) {
+      const Key& k = cells[size_t(i)];
+      int8_t f = 0;
+      if (k.level < max_level_ && meets(k))
+        f = 1;
+      else if (k.level > 0 && !meets(parent(k)))
+        f = -1;
+      flags[i] = f;
+    }
+  });
 }
 
 }  // namespace ader

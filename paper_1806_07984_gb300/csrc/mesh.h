@@ -62,6 +62,7 @@ class KeyMap {
       if (keys_[i] == kEmpty) return nullptr;
     }
   }
+  int32_t* find_mut(uint64_t k) { return const_cast<int32_t*>(static_cast<const KeyMap*>(this)->find(k)); }
   bool count(uint64_t k) const { return find(k) != nullptr; }
   void erase(uint64_t k) {
     for (size_t i = slot(k);; i = (i + 1) & (keys_.size() - 1)) {
@@ -201,15 +202,18 @@ class Tree {
   int max_level_across(const Key& k, int dir, int side) const;
   int max_level_below_face(const Key& k, int dir, int side) const;
   void split(const Key& k);
-  void rebuild_refined();
-  void order_cells(std::vector<Key>* out) const;
-  void dfs(const Key& k, std::vector<Key>* out) const;
+  // Depth-first leaf order from the base cells; stores each leaf's position
+  // as its value in leaves_ (the index lookups of build() and remesh()).
+  void order_cells(std::vector<Key>* out);
+  void dfs(const Key& k, std::vector<Key>* out, std::vector<int32_t*>* slots);
+  bool plan_by_walk(const std::vector<Key>& old_cells, std::vector<TransferItem>* plan,
+                    std::vector<int32_t>* coarsen_children) const;
 
   int dim_ = 0;
   int base_[3] = {1, 1, 1};
   int max_level_ = 0;
-  KeyMap leaves_;
-  KeyMap refined_;
+  KeyMap leaves_;   // leaf keys -> position in `cells` (set by build())
+  KeyMap refined_;  // keys of refined (non-leaf) nodes, kept in step with leaves_
   std::string error_;
 };
 
