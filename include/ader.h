@@ -31,6 +31,9 @@
  *   - Numerical failures inside kernels (non-finite predictor output, rho <= 0
  *     or p <= 0, non-finite CFL rate) set bits of a device status word that
  *     ader_status_word() reads after synchronising.
+ *   - ADER_ERR_OOM or ADER_ERR_CUDA from a call that may grow the context's
+ *     cell buffers (ader_init, ader_remesh) can leave some of them released:
+ *     the only call such a context accepts afterwards is ader_destroy.
  *
  * Data layout (FP64 throughout at the boundary; c = cell, m = nvar,
  * n = order + 1 Gauss-Legendre nodes per direction, node index with x fastest,
