@@ -95,6 +95,13 @@ def test_mesh_parity_deep_2d(A):
     assert drive(A, 2, 3, 3, centers, 0.02) > 9
 
 
+def test_mesh_parity_threaded(A):
+    """Meshes large enough (> 8,192 leaves) for the multi-threaded host passes
+    (depth-first order, face sweep, sphere flags) still equal the oracle's."""
+    assert drive(A, 2, 45, 2, [(0.5, 0.5), (0.5, 0.5), (0.58, 0.52)], 0.2) > 16384
+    assert drive(A, 3, 20, 1, [(0.5, 0.5, 0.5), (0.6, 0.55, 0.5)], 0.2) > 16384
+
+
 def test_mesh_single_cell(A):
     lm = A.ader_mesh_create(3, (1, 1, 1), 1)
     try:
