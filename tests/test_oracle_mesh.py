@@ -143,6 +143,29 @@ def test_coarsen_blocked_by_balance():
     assert len(m.cells) == n_before
 
 
+def test_coarsen_blocked_by_finer_neighbour():
+    """A complete family of flagged leaves stays refined while a leaf two
+    levels finer than its parent touches one of the parent's faces: cell
+    (0,(1,1)) is refined, and the level-1 cell left of it, (1,(2,4)), is
+    refined again, so its level-2 children touch the family; coarsening the
+    family would put level 0 next to level 2."""
+    m = meshmod.Mesh(2, (3, 3), 3)
+    B = basis.Basis(1)
+    u = np.zeros((9, 1, 2, 2))
+    u = m.remesh(u, [1 if k in ((0, (1, 1)), (0, (0, 1))) else 0 for k in m.cells], B)
+    u = m.remesh(u, [1 if k == (1, (2, 4)) else 0 for k in m.cells], B)
+    assert (2, (8, 13)) in m.leaves and (1, (3, 4)) in m.leaves
+    family = [k for k in m.cells if k[0] == 1 and k[1][0] // 3 == 1 and k[1][1] // 3 == 1]
+    assert len(family) == 9
+    before = sorted(m.cells)
+    u = m.remesh(u, [-1 if k in family else 0 for k in m.cells], B)
+    assert sorted(m.cells) == before
+    # and once the finer cells are gone, the same family coarsens
+    u = m.remesh(u, [-1 if k[0] == 2 else 0 for k in m.cells], B)
+    u = m.remesh(u, [-1 if k in family else 0 for k in m.cells], B)
+    assert (0, (1, 1)) in m.leaves
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_prolong_face_equals_extrapolated_prolong_volume(dim):
     """Face-only prolongation (virtual-cell faces) equals extrapolating the

@@ -112,6 +112,38 @@ def test_rusanov_mirror_symmetry():
     assert np.allclose(F, -flip * Fm, atol=1e-14)
 
 
+def test_rusanov_speed_bounds_every_wave_on_the_face():
+    """Sec. 2.4: one estimate of the largest eigenvalue per face.  On Euler
+    faces whose nodes carry different states, the dissipation coefficient
+    implied by F* (from F* - (F_L + F_R)/2 = -s (Q_R - Q_L)/2) is one number per
+    face, no smaller than any local wave speed |v_d| + c on either side (the
+    bound a monotone local Lax-Friedrichs flux needs) and no larger than the
+    largest of them."""
+    dim, d = 3, 1
+    pde = pdes.Euler(dim)
+    rng = np.random.default_rng(13)
+    QL = np.moveaxis(workloads.random_euler(rng, dim, (5, 9), amp=0.3), 0, 1)
+    QR = np.moveaxis(workloads.random_euler(rng, dim, (5, 9), amp=0.3), 0, 1)
+    QR[2, :, 4] = pde.primitive_to_conserved(1.0, [0.5, 3.0, 0.2], 1.0)   # one fast node, v_y = 3
+
+    def fl(q):
+        return np.moveaxis(pde.flux(np.moveaxis(q, 1, 0), d), 0, 1)
+
+    F = ader.rusanov(QL, fl(QL), QR, fl(QR), pde, d)
+    jump = QR - QL
+    ok = np.abs(jump) > 1e-2             # entries where s is well determined
+    s = -2.0 * (F - 0.5 * (fl(QL) + fl(QR)))[ok] / jump[ok]
+    face = np.broadcast_to(np.arange(5)[:, None, None], jump.shape)[ok]
+    lam = np.maximum(pde.max_speed(np.moveaxis(QL, 1, 0), d), pde.max_speed(np.moveaxis(QR, 1, 0), d))
+    for f in range(5):
+        sf = s[face == f]
+        assert len(sf) > 20
+        assert np.allclose(sf, sf[0], rtol=1e-8)
+        assert sf.min() >= lam[f].max() * (1 - 1e-8)
+        assert sf.max() <= lam[f].max() * (1 + 1e-8)
+    assert lam[2].max() > 1.5 * np.delete(lam[2], 4).max()
+
+
 def test_cfl_rate_by_hand():
     """Uniform state: the rate is sum_d (|v_d| + c) / h_d, computed by hand."""
     pde = pdes.Euler(2)

@@ -29,27 +29,28 @@ def test_free_stream_predictor(dim, N):
 
 @pytest.mark.parametrize("N", [2, 3, 5, 7])
 def test_picard_entropy_wave_is_exact(N):
-    """Euler data with uniform v and p and a density polynomial of degree N in
-    x: the exact flow translates rho with v_x, which is a degree-N polynomial
-    in time at every node, so the DG-in-time fixed point is exact and Picard
-    reaches it in N + 1 iterations."""
+    """Euler data with uniform v and p and a density f(x) + g(y) with f, g
+    polynomials of degree N, on a cell with h_x != h_y: the exact flow
+    translates rho with v, a degree-N polynomial in time at every node, so the
+    DG-in-time fixed point is exact and Picard reaches it in N + 1 iterations
+    (a derivative scaled by the wrong cell width fails)."""
     B = basis.Basis(N)
     dim = 2
     pde = pdes.Euler(dim)
     h = np.array([[0.2, 0.3]])
     vx, vy, p = 0.7, -0.4, 1.3
     dt = 0.9 / (2 * N + 1) * 0.2 / 2.5      # the CFL step of the scheme
-    coeff = np.random.default_rng(N).uniform(-0.1, 0.1, size=N + 1)
+    cx, cy = np.random.default_rng(N).uniform(-0.1, 0.1, size=(2, N + 1))
 
-    def rho_of(x):
-        return 1.0 + sum(c * x ** k for k, c in enumerate(coeff))
+    def rho_of(x, y):
+        return 1.0 + sum(c * x ** k for k, c in enumerate(cx)) + sum(c * y ** k for k, c in enumerate(cy))
 
     X = cell_coords(B, dim, h[0], np.array([0.1, 0.0]))
-    u = pde.primitive_to_conserved(rho_of(X[0]), [vx, vy], p)[np.newaxis]
+    u = pde.primitive_to_conserved(rho_of(X[0], X[1]), [vx, vy], p)[np.newaxis]
     q = ader.picard_predictor(u, h, dt, pde, B, N + 1)
     for k in range(B.n):
         t = B.xi[k] * dt
-        exact = pde.primitive_to_conserved(rho_of(X[0] - vx * t), [vx, vy], p)
+        exact = pde.primitive_to_conserved(rho_of(X[0] - vx * t, X[1] - vy * t), [vx, vy], p)
         assert np.allclose(q[0, k], exact, atol=1e-13, rtol=0)
 
 
