@@ -207,6 +207,47 @@ def test_detection_rules():
     assert lmt[9] and lmt.sum() == 1
 
 
+def test_detection_admissibility_alone():
+    """With the candidate equal to u(T) the maximum principle holds trivially,
+    so only admissibility can flag: a node with rho > 0 but p < 0, and a cell
+    whose nodal densities are all positive while the polynomial's average over
+    an edge subcell is negative."""
+    P = pdes.Euler(2)
+    q0 = P.primitive_to_conserved(1.0, [0.0, 0.0], 1.0)
+    m, B, u = _uniform(2, 4, 3, q0)
+    sc, nb = lim.Subcells(B), lim.neighbors(m)
+    cand = u.copy()
+    cand[3, 1, 2, 1] = 3.0                 # rho v_x = 3 at one node: kinetic energy 4.5 > E = 2.5
+    assert P.pressure(cand[3, :, 2, 1]) < 0 < cand[3, 0, 2, 1]
+    lmt, _ = lim.detect(P, cand, cand, sc, nb)
+    assert lmt[3] and lmt.sum() == 1
+    cand = u.copy()
+    eps = 1e-3
+    cand[7, 0] = np.array([1.0, eps, eps, 1.0])[np.newaxis, :]   # rho along x, at rest: p stays 1
+    v = lim.averages(cand[7:8], sc)[0, 0]
+    assert (cand[7, 0] > 0).all() and v.min() < 0
+    lmt, _ = lim.detect(P, cand, cand, sc, nb)
+    assert lmt[7] and lmt.sum() == 1
+
+
+def test_detection_bounds_include_the_neighbours():
+    """The relaxed maximum principle takes its bounds over the cell and its
+    face neighbours: a candidate that leaves its own cell's range but stays
+    inside a neighbour's is accepted, in both directions."""
+    P = pdes.Euler(2)
+    q0 = P.primitive_to_conserved(1.0, [0.2, 0.1], 1.0)
+    m, B, u = _uniform(2, 4, 3, q0)
+    sc, nb = lim.Subcells(B), lim.neighbors(m)
+    for sign in (-1.0, 1.0):
+        old = u.copy()
+        old[6, 0] += sign * 0.5            # cell 6 shares a face with cell 5
+        cand = old.copy()
+        cand[5, 0] += sign * 0.3
+        assert not lim.detect(P, old, cand, sc, nb)[0][5]
+        cand[5, 0] = old[5, 0] + sign * 0.6
+        assert lim.detect(P, old, cand, sc, nb)[0][5]
+
+
 def test_no_limiting_across_transitions():
     """A forced cell with a non-conforming face keeps its DG candidate."""
     m = refined_mesh(2, 9, 1, (0.5, 0.5), 0.1)
@@ -275,3 +316,18 @@ def test_refine_flags_around_troubled_cells():
     # symmetric neighbour relation, 2d faces per cell at least
     for i in range(len(m.cells)):
         assert all(i in nb[j] for j in nb[i]) and len(nb[i]) >= 4
+
+
+def test_refine_flags_at_the_finest_level():
+    """A troubled cell already at the finest level keeps its level (flag 0),
+    like its finest-level neighbours; a coarser troubled neighbourhood refines."""
+    m = refined_mesh(2, 9, 2, (0.5, 0.5), 0.1)
+    levels = np.array([k[0] for k in m.cells])
+    fine = int(np.flatnonzero(levels == m.max_level)[0])
+    troubled = np.zeros(len(m.cells), dtype=bool)
+    troubled[fine] = True
+    flags = lim.refine_flags(m, troubled)
+    assert flags[fine] == 0
+    nb = lim.face_neighbours(m)
+    for j in nb[fine]:
+        assert flags[j] == (1 if levels[j] < m.max_level else 0)

@@ -211,6 +211,37 @@ def test_gradient_indicator_of_linear_and_quadratic_fields():
                            for hh, k in zip(h[:, 0], m.cells)]
 
 
+def test_gradient_indicator_anisotropic_cells():
+    """On cells with h_x = 3 h_y the weight is the larger width:
+    eta = h_max |grad q| = 5 h_x for q = 3x - 4y."""
+    from oracle import criterion
+    B = basis.Basis(2)
+    m = meshmod.Mesh(2, (3, 9), 0)
+    X = m.node_coords(B.xi)
+    u = (3.0 * X[0] - 4.0 * X[1])[:, np.newaxis]
+    h = m.cell_widths()
+    assert np.allclose(h[:, 0], 3.0 * h[:, 1])
+    assert np.allclose(criterion.gradient_indicator(u, h, B, 0), 5.0 * h[:, 0], rtol=1e-12)
+
+
+def test_sphere_flags_periodic_distance_and_coarsening_rule():
+    """The ball is measured with the periodic distance (a ball at x = 0.02
+    reaches the last column of cells), and a leaf coarsens only when its
+    parent's box misses the ball (a sibling of a cell that meets it stays)."""
+    m = meshmod.Mesh(2, (9, 9), 1)
+    fl = meshmod.sphere_flags(m, (0.02, 0.5), 0.05)
+    assert fl[m.index[(0, (8, 4))]] == 1 and fl[m.index[(0, (0, 4))]] == 1
+    assert fl[m.index[(0, (7, 4))]] == 0
+    B = basis.Basis(1)
+    m.remesh(np.zeros((81, 1, 2, 2)), fl, B)
+    # the ball now moves so that it meets only the left column of the family of (0, (0, 4))
+    fl = meshmod.sphere_flags(m, (0.0, 0.5), 0.02)
+    sib = m.index[(1, (2, 13))]           # right column of that family: its own box misses the ball
+    assert fl[sib] == 0
+    gone = meshmod.sphere_flags(m, (0.5, 0.9), 0.02)
+    assert gone[sib] == -1
+
+
 def test_hessian_indicator_closed_forms():
     """eta = h^2 |H q|_F against closed forms on an anisotropic 2-level mesh
     (h_x != h_y, so a derivative taken along the wrong axis or divided by the

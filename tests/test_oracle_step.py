@@ -154,6 +154,36 @@ def test_convergence_isentropic_vortex():
     assert np.all(rates > N + 0.4), (errs, rates)
 
 
+@pytest.mark.parametrize("N", [2, 3])
+def test_full_step_obeys_the_von_neumann_limit(N):
+    """The stability module assembles its own 1D amplification matrix; the
+    full 2D step (mesh, faces, Rusanov, corrector) on acoustic data that vary
+    in x only is a pair of advection problems with speed 1, so it must stay
+    bounded at 0.9 nu_N and blow up at 1.2 nu_N (Courant number dt / h_x)."""
+    from oracle import stability
+    B = basis.Basis(N)
+    P = pdes.Acoustics(2)
+    m = meshmod.Mesh(2, (12, 1), 0)
+    rng = np.random.default_rng(40 + N)
+    u = np.zeros((12, 3, B.n, B.n))
+    u[:] = rng.standard_normal((12, 3, 1, B.n))       # uniform in y
+    hx = m.cell_widths()[0, 0]
+    nu = stability.stability_limit(N)
+    W = np.outer(B.w, B.w)
+
+    def energy(x):                                    # GL-weighted L2 norm squared
+        return float((x * x * W).sum())
+
+    norms = {}
+    for factor in (0.9, 1.2):
+        v = u.copy()
+        for _ in range(40):
+            v = stepmod.step(m, v, factor * nu * hx, P, B).u
+        norms[factor] = np.sqrt(energy(v) / energy(u))
+    assert norms[0.9] <= 1.0 + 1e-10
+    assert norms[1.2] > 1e3
+
+
 def test_acoustics_energy_does_not_grow(amr2d):
     """Linear acoustics with Rusanov dissipation: the discrete energy
     sum W (p^2 + |v|^2) does not grow over a step, also across AMR."""
