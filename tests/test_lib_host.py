@@ -19,6 +19,16 @@ def A():
     return ader
 
 
+def test_missing_library_fails_loudly(A, monkeypatch, tmp_path):
+    """Without libader.so every entry point raises: there is no fallback."""
+    monkeypatch.setattr(A, "LIB_PATH", str(tmp_path / "libader.so"))
+    monkeypatch.setattr(A, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        A.lib()
+    with pytest.raises(RuntimeError):
+        A.ader_mesh_create(2, (3, 3), 1)
+
+
 def test_exports_match_header(A):
     header = open(os.path.join(ROOT, "include", "ader.h")).read()
     declared = set(re.findall(r"\b(ader_\w+)\s*\(", header))
