@@ -390,10 +390,15 @@ ader_status ader_batch_launch_count(ader_batch* b, int64_t* out);
  *   u_dev      device state u[c][var][node] (layout as above), ncells cells
  *   level_dev  device int8 level per cell, 0 <= level < 8 (other values make
  *              the result NaN); h_d = (hi[d] - lo[d]) / (base[d] 3^level)
- *   dt_dev     device double receiving dt (NaN if a state is non-physical)
+ *   dt_dev     device double receiving dt; NaN if a state is non-physical
+ *              or if the maximum rate is zero or not finite (the cases in
+ *              which the context path sets its non-finite-rate status bit)
  * Sizes: 1 <= ncells <= ADER_DT_STATIC_MAX_CELLS, else ADER_ERR_ARG.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture.  The kept address belongs to the device's
+ * primary context: after cudaDeviceReset on that device, do not call this
+ * entry point again in the same process.  All calls
  * share the one array and each call overwrites the slots it reads, so calls
  * that overlap on the GPU (different streams, or several host threads) race:
  * serialise them. */

@@ -320,18 +320,36 @@ __global__ void restrict_kernel(const RiemannArgs a) {
   }
 }
 
+// Maximum over the lanes of the calling warp that exist, valid in lane 0.
+// A CTA whose size is not a multiple of 32 (216 threads at 3D N=5, 250 at
+// 3D N=4, 252 at 2D N=5) ends in a partial warp; its shuffles name only the
+// existing lanes and discard what a shuffle from past the last one returns.
+// Every existing lane of the warp must call this (1D CTAs).
+__device__ __forceinline__ double warp_max_lane0(double v) {
+  const int lane = int(threadIdx.x) & 31;
+  const int width = min(32, int(blockDim.x) - (int(threadIdx.x) - lane));
+  const unsigned mask = width >= 32 ? 0xffffffffu : ((1u << width) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_down_sync(mask, v, o);
+    if (lane + o < width) v = fmax(v, x);
+  }
+  return v;
+}
+
 // CTA-wide max, one atomicMax on the FP64 bit pattern (non-negative doubles
-// order like their unsigned bit patterns; NaN sorts above +inf).
+// order like their unsigned bit patterns; NaN sorts above +inf).  Any CTA
+// size from 1 to 1024 threads; every thread of the CTA must call it.
 __device__ __forceinline__ void block_max_to(double v, unsigned long long* out) {
   __shared__ double red[32];
-  v = warp_max(v);
+  v = warp_max_lane0(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
     const int nw = (blockDim.x + 31) >> 5;
     double x = lane < nw ? red[lane] : 0.0;
-    x = warp_max(x);
+    x = warp_max_lane0(x);
     if (lane == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(x)));
   }
 }

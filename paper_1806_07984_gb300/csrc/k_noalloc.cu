@@ -31,6 +31,7 @@ __device__ __forceinline__ double nan_max(double a, double b) {
   return (a != a || b != b) ? __longlong_as_double(0x7ff8000000000000ll) : fmax(a, b);
 }
 
+// Butterfly maximum over a full warp (every CTA of this file is whole warps).
 __device__ __forceinline__ double warp_nan_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -43,8 +44,16 @@ struct InvH {
   double v[kMaxLevels][3];
 };
 
+// Threads of the first pass: the shape's threads rounded up to whole warps.
+// The extra lanes hold the neutral rate 0 and load nothing, so every warp of
+// the CTA is full and the butterfly shuffles read only existing lanes.
+template <int DIM, int N>
+struct PartialsShape {
+  static constexpr int THREADS = (PredictShape<DIM, N>::THREADS + 31) / 32 * 32;
+};
+
 template <int DIM, int N, class PDE>
-__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
+__global__ void __launch_bounds__(PartialsShape<DIM, N>::THREADS)
     dt_partials_kernel(const double* u, const int8_t* level, int64_t ncells, double gamma,
                        const InvH inv_h, double* partials) {
   using SH = PredictShape<DIM, N>;
@@ -54,7 +63,7 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
   const int node = tid - cl * NS;
   const int64_t cell = int64_t(blockIdx.x) * CPB + cl;
   double rate = 0.0;
-  if (cell < ncells) {
+  if (tid < SH::THREADS && cell < ncells) {
     const int lv_raw = int(level[cell]);
     const bool lv_ok = lv_raw >= 0 && lv_raw < kMaxLevels;
     const int lv = lv_ok ? lv_raw : 0;
@@ -83,7 +92,8 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS)
   }
 }
 
-// Second pass: one CTA reduces the partials and writes dt.
+// Second pass: one CTA of 1024 threads (whole warps) reduces the partials
+// and writes dt.
 __global__ void dt_finish_kernel(const double* partials, int64_t count, double cfl, double* dt) {
   double m = 0.0;
   for (int64_t i = threadIdx.x; i < count; i += blockDim.x) m = nan_max(m, partials[i]);
@@ -95,7 +105,9 @@ __global__ void dt_finish_kernel(const double* partials, int64_t count, double c
   if (warp == 0) {
     double x = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
     x = warp_nan_max(x);
-    if (lane == 0) *dt = cfl / x;
+    // a zero, infinite or NaN maximum rate has no time step: NaN, like the
+    // non-finite-rate failure of the context path
+    if (lane == 0) *dt = (x > 0.0 && isfinite(x)) ? cfl / x : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -107,13 +119,15 @@ cudaError_t launch_partials(int order, const double* u, const int8_t* level, int
     constexpr int N = decltype(Nc)::value;
     using SH = PredictShape<DIM, N>;
     *nblocks = (ncells + SH::CPB - 1) / SH::CPB;
-    dt_partials_kernel<DIM, N, PDE><<<unsigned(*nblocks), SH::THREADS, 0, s>>>(
+    dt_partials_kernel<DIM, N, PDE><<<unsigned(*nblocks), PartialsShape<DIM, N>::THREADS, 0, s>>>(
         u, level, ncells, gamma, inv_h, partials);
     return cudaGetLastError();
   });
 }
 
-// Device address of g_dt_partials for the current device, looked up once.
+// Device address of g_dt_partials for the current device, looked up once per
+// device and kept for the life of the process (it names the primary
+// context's copy of the array, so it is stale after cudaDeviceReset).
 cudaError_t partials_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -14,6 +14,20 @@ def rel_l2(a, b):
     return np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0)
 
 
+def rel_max(a, b):
+    """Per-element bound: max |a - b| / max |b| (one wrong value among many
+    cannot hide in the L2 norm of the whole field)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.abs(b).max() if b.size else 0.0
+    return np.abs(a - b).max() / (den if den > 0 else 1.0) if b.size else 0.0
+
+
+def close_fields(a, b, tol):
+    """Relative L2 <= tol and the per-element bound <= 10 tol."""
+    return rel_l2(a, b) < tol and rel_max(a, b) <= 10.0 * tol
+
+
 def lib_keys(solver):
     cells = solver.cells()
     d = solver.dim

@@ -33,7 +33,9 @@ def _static_dt(A, solver, u_dev, lv_dev, torch):
     return dt.item()
 
 
-@pytest.mark.parametrize("dim,order", [(3, 3), (2, 5)])
+# 3D N=3: 256-thread CTAs; 2D N=5: 252 and 3D N=5: 216 threads, whose last
+# warp is partial; 3D N=7: one cell of 512 nodes per CTA.
+@pytest.mark.parametrize("dim,order", [(3, 3), (2, 5), (3, 5), (3, 7)])
 def test_static_dt_matches_context_dt_twice(dim, order):
     import torch
     from paper_1806_07984_gb300 import Solver, ader as A
@@ -66,3 +68,42 @@ def test_static_dt_rejects_too_many_cells():
                                  A.ADER_DT_STATIC_MAX_CELLS + 1, dummy.data_ptr(), lv.data_ptr(),
                                  dummy.data_ptr())
     assert e.value.status == -1
+
+
+def _bubble_solver(dim, order):
+    from paper_1806_07984_gb300 import Solver
+    s = Solver(dim, order, "euler", base=(5, 5, 5) if dim == 3 else (9, 9, 1), max_level=1,
+               cfl=workloads.ADER_CFL[order])
+    s.remesh(s.sphere_flags((0.5, 0.5, 0.5)[:dim], 0.2))
+    X = s.node_coords()
+    u = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X, sigma=0.1), 0, 1))
+    s.set_state(u)
+    return s, u
+
+
+@pytest.mark.parametrize("dim,order", [(3, 5), (2, 5)])
+def test_static_dt_is_nan_for_negative_pressure(dim, order):
+    import torch
+    from paper_1806_07984_gb300 import ader as A
+    s, u = _bubble_solver(dim, order)
+    bad = u.copy()
+    flat = bad.reshape(bad.shape[0], bad.shape[1], -1)
+    flat[s.ncells // 2, dim + 1, 3] = -1.0       # E < kinetic energy: p < 0
+    u_dev = torch.from_numpy(bad).to(s.device)
+    assert np.isnan(_static_dt(A, s, u_dev, _levels(s, torch), torch))
+    # the same call on the good state is finite again (nothing sticks)
+    got = _static_dt(A, s, torch.from_numpy(u).to(s.device), _levels(s, torch), torch)
+    assert abs(got - s.compute_dt().item()) <= TOL * got
+    s.close()
+
+
+def test_static_dt_is_nan_for_level_out_of_range():
+    import torch
+    from paper_1806_07984_gb300 import ader as A
+    s, _ = _bubble_solver(3, 3)
+    lv = _levels(s, torch)
+    lv[s.ncells // 3] = 8
+    assert np.isnan(_static_dt(A, s, s.get_state(), lv, torch))
+    lv[s.ncells // 3] = -1
+    assert np.isnan(_static_dt(A, s, s.get_state(), lv, torch))
+    s.close()
