@@ -323,6 +323,74 @@ ader_status ader_sample_adjoint(ader_ctx* ctx, int npts, const int32_t* cells,
 /* Number of kernel launches this context has enqueued so far. */
 ader_status ader_launch_count(ader_ctx* ctx, int64_t* out);
 
+/* ---- Domain decomposition (Sec. 3, distributed memory) -------------------
+ * The paper splits the space-filling-curve order of the cells into
+ * non-overlapping contiguous partitions, solves the Riemann problems on faces
+ * between two partitions on both sides, and sends the predictor results of
+ * the cells along a partition boundary to the neighbour once per step (those
+ * cells are skeleton cells, so that their predictions come first and the
+ * enclave predictions hide the exchange).  Here the depth-first cell order is
+ * cut into nranks ranges on base-cell boundaries (every family of siblings in
+ * one range) with cell counts as even as that allows.  Each rank's context
+ * keeps the whole tree on the host (flags and remeshing need no exchange) and
+ * on the device only its owned cells plus ghosts: every cell that shares a
+ * conforming face or a parent face family with an owned cell.
+ *
+ * Partitioned context, per step (the caller moves the buffers between ranks:
+ * device copies, MPI, NCCL or torch.distributed):
+ *   ader_predict(SKELETON); for each peer: ader_halo_pack
+ *   ader_predict(ENCLAVE)                     (overlaps the exchange)
+ *   exchange the packed buffers; for each peer: ader_halo_unpack
+ *   ader_riemann(ALL); ader_correct(dt, dt_local)
+ *   dt_next = min over ranks of dt_local      (= cfl / max of the rates)
+ * The result equals the unpartitioned step cell for cell, bit for bit.
+ * In a partitioned context, state arrays (ader_set_state, ader_get_state,
+ * ader_get_field of u and u*) hold the owned cells, ader_mesh_info counts and
+ * ader_mesh_cells lists them, and face fields hold owned then ghost cells;
+ * flags arrays (ader_remesh, ader_classify, ader_sphere_flags) have one entry
+ * per cell of the whole mesh (ader_dd_info's nglobal), identical on every
+ * rank.  ader_step, the limiter and the adjoint step are not available. */
+
+/* Partition the context's current mesh into nranks ranges and keep rank
+ * `rank` (0 <= rank < nranks); the owned rows of the current state are kept.
+ * nranks = 1 leaves the context whole.  Synchronises the device.
+ * ADER_ERR_ARG if the context is partitioned already, has the limiter, or
+ * nranks exceeds the number of base cells. */
+ader_status ader_partition(ader_ctx* ctx, int nranks, int rank);
+
+/* Partition facts (any may be NULL): ranks, this rank, cells of the whole
+ * mesh, first owned cell (index into the whole mesh's order), owned cells,
+ * ghost cells.  An unpartitioned context reports one rank owning every cell. */
+ader_status ader_dd_info(ader_ctx* ctx, int* nranks, int* rank, int64_t* nglobal, int64_t* first,
+                         int64_t* nowned, int64_t* nghost);
+
+/* The nranks + 1 cut points in the whole mesh's cell order (rank r owns
+ * [cuts[r], cuts[r+1])). */
+ader_status ader_dd_cuts(ader_ctx* ctx, int64_t* cuts);
+
+/* Halo exchange with `peer`: sizes in doubles of the buffer this rank sends
+ * and of the one it receives (equal to the peer's send size); 0 for a peer
+ * that shares no face.  ader_halo_pack writes the predictor's face data
+ * (Q-bar and F-bar of each face slot the peer needs, in an order both sides
+ * derive from the mesh) into buf_dev; ader_halo_unpack copies a received
+ * buffer into the ghosts' face slots.  Device buffers owned by the caller,
+ * enqueued on `stream`.  ADER_ERR_ARG for an unpartitioned context or a peer
+ * outside [0, nranks). */
+ader_status ader_halo_size(ader_ctx* ctx, int peer, int64_t* send_doubles, int64_t* recv_doubles);
+ader_status ader_halo_pack(ader_ctx* ctx, int peer, double* buf_dev, void* stream);
+ader_status ader_halo_unpack(ader_ctx* ctx, int peer, const double* buf_dev, void* stream);
+
+/* State migration after ader_remesh on a partitioned context.  The remesh
+ * transfers the state of the rank's old base-cell range, rebalances the cuts
+ * for the new mesh, and keeps the cells it still owns; the cells that change
+ * owner go from their old to their new owner through these calls (sizes in
+ * doubles; pack reads the rank's transferred cells, unpack writes owned
+ * cells).  Every rank must unpack from every peer before the next step.  Valid
+ * until the next remesh; sizes are 0 when no remesh has run. */
+ader_status ader_migrate_size(ader_ctx* ctx, int peer, int64_t* send_doubles, int64_t* recv_doubles);
+ader_status ader_migrate_pack(ader_ctx* ctx, int peer, double* buf_dev, void* stream);
+ader_status ader_migrate_unpack(ader_ctx* ctx, int peer, const double* buf_dev, void* stream);
+
 /* ---- Batched instances ---------------------------------------------------
  * Many independent problems of uneven sizes and orders advanced together
  * (Algorithm 1 per instance, each instance with its own global time step).
@@ -441,6 +509,23 @@ ader_status ader_mesh_sphere_flags(ader_mesh* mesh, const double center[3], doub
 /* The remesh rule of ader_limiter_refine_flags for a given troubled set
  * (troubled[c] != 0, one byte per cell in mesh order). */
 ader_status ader_mesh_refine_around(ader_mesh* mesh, const uint8_t* troubled, int8_t* flags);
+
+/* The partition of ader_partition on the host mesh: sizes[9] receives the
+ * first owned cell, owned cells, ghosts, local conforming faces, those
+ * between two owned skeleton cells (listed first), local parent faces,
+ * skeleton cells, and the send and receive entries over all peers.
+ * ader_mesh_subdomain then fills (any may be NULL): cuts[nranks + 1], ghosts
+ * (index in the whole mesh of ghost g = local cell nowned + g), conf_out
+ * (left, right, dir in local cells), parents_out (coarse, dir, coarse side)
+ * with child_out (3^(dim-1) fine cells each), skel_out (local skeleton
+ * cells), and per peer the exchange entries local_cell * 2 dim + (2 dir +
+ * side) at send_out[send_off[q] .. send_off[q+1]) and recv_out likewise.
+ * ader_mesh_adapt discards the partition. */
+ader_status ader_mesh_partition(ader_mesh* mesh, int nranks, int rank, int64_t* sizes);
+ader_status ader_mesh_subdomain(ader_mesh* mesh, int64_t* cuts, int32_t* ghosts, int32_t* conf_out,
+                                int32_t* parents_out, int32_t* child_out, int32_t* skel_out,
+                                int64_t* send_off, int32_t* send_out, int64_t* recv_off,
+                                int32_t* recv_out);
 
 /* The enclave pipeline of ader_step for K chunks (see ader_step) on the host
  * mesh, whose skeleton is its transition cells: fills chunk_off[K+1]

@@ -41,7 +41,10 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_sample", "ader_sample_adjoint", "ader_gradient_flags", "ader_gradient_indicator",
            "ader_limiter_flags",
            "ader_limiter_force", "ader_limiter_refine_flags", "ader_mesh_refine_around",
-           "ader_mesh_pipeline"]
+           "ader_mesh_pipeline", "ader_partition", "ader_dd_info", "ader_dd_cuts",
+           "ader_halo_size", "ader_halo_pack", "ader_halo_unpack", "ader_migrate_size",
+           "ader_migrate_pack", "ader_migrate_unpack", "ader_mesh_partition",
+           "ader_mesh_subdomain"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -136,6 +139,19 @@ def lib():
         "ader_gradient_indicator": ([_vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
         "ader_sample": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
         "ader_sample_adjoint": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
+                                ctypes.c_int),
+        "ader_partition": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "ader_dd_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _i64p, _i64p,
+                          _i64p, _i64p], ctypes.c_int),
+        "ader_dd_cuts": ([_vp, _vp], ctypes.c_int),
+        "ader_halo_size": ([_vp, ctypes.c_int, _i64p, _i64p], ctypes.c_int),
+        "ader_halo_pack": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_halo_unpack": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_migrate_size": ([_vp, ctypes.c_int, _i64p, _i64p], ctypes.c_int),
+        "ader_migrate_pack": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_migrate_unpack": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_mesh_partition": ([_vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+        "ader_mesh_subdomain": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
                                 ctypes.c_int),
         "ader_compute_dt_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
@@ -251,7 +267,7 @@ def ader_classify(ctx, flags=None):
 
 
 def ader_sphere_flags(ctx, center, radius):
-    ncells = ader_mesh_info(ctx)[0]
+    ncells = ader_dd_info(ctx)[2]          # whole mesh (also when partitioned)
     c = np.zeros(3, dtype=np.float64)
     c[:len(center)] = center
     out = np.zeros(ncells, dtype=np.int8)
@@ -496,3 +512,71 @@ def ader_mesh_pipeline(mesh, K):
     _check(None, lib().ader_mesh_pipeline(mesh, K, _ptr(chunk), _ptr(face), _ptr(corr), _ptr(cells),
                                           _ptr(conf), ctypes.byref(nsk)), "ader_mesh_pipeline")
     return chunk, face, corr, cells, conf, nsk.value
+
+
+# ---- domain decomposition ---------------------------------------------------
+def ader_partition(ctx, nranks, rank):
+    _check(ctx, lib().ader_partition(ctx, nranks, rank), "ader_partition")
+
+
+def ader_dd_info(ctx):
+    """(nranks, rank, nglobal, first, nowned, nghost)."""
+    r = [ctypes.c_int(), ctypes.c_int()]
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(ctx, lib().ader_dd_info(ctx, *[ctypes.byref(x) for x in r + v]), "ader_dd_info")
+    return tuple(x.value for x in r + v)
+
+
+def ader_dd_cuts(ctx):
+    cuts = np.zeros(ader_dd_info(ctx)[0] + 1, dtype=np.int64)
+    _check(ctx, lib().ader_dd_cuts(ctx, _ptr(cuts)), "ader_dd_cuts")
+    return cuts
+
+
+def ader_halo_size(ctx, peer):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib().ader_halo_size(ctx, peer, ctypes.byref(a), ctypes.byref(b)), "ader_halo_size")
+    return a.value, b.value
+
+
+def ader_halo_pack(ctx, peer, buf, stream=None):
+    _check(ctx, lib().ader_halo_pack(ctx, peer, _ptr(buf), stream), "ader_halo_pack")
+
+
+def ader_halo_unpack(ctx, peer, buf, stream=None):
+    _check(ctx, lib().ader_halo_unpack(ctx, peer, _ptr(buf), stream), "ader_halo_unpack")
+
+
+def ader_migrate_size(ctx, peer):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib().ader_migrate_size(ctx, peer, ctypes.byref(a), ctypes.byref(b)),
+           "ader_migrate_size")
+    return a.value, b.value
+
+
+def ader_migrate_pack(ctx, peer, buf, stream=None):
+    _check(ctx, lib().ader_migrate_pack(ctx, peer, _ptr(buf), stream), "ader_migrate_pack")
+
+
+def ader_migrate_unpack(ctx, peer, buf, stream=None):
+    _check(ctx, lib().ader_migrate_unpack(ctx, peer, _ptr(buf), stream), "ader_migrate_unpack")
+
+
+def ader_mesh_partition(mesh, nranks, rank, dim):
+    """Host partition of a mesh handle: a dict of the sub-domain lists (see
+    include/ader.h) for rank ``rank`` of ``nranks``."""
+    sz = np.zeros(9, dtype=np.int64)
+    _check(None, lib().ader_mesh_partition(mesh, nranks, rank, _ptr(sz)), "ader_mesh_partition")
+    first, nown, nghost, nconf, nconf_skel, npar, nskel, nsend, nrecv = (int(x) for x in sz)
+    out = dict(first=first, nowned=nown, nghost=nghost, n_conf_skeleton=nconf_skel,
+               cuts=np.zeros(nranks + 1, dtype=np.int64), ghosts=np.zeros(nghost, dtype=np.int32),
+               conf=np.zeros((nconf, 3), dtype=np.int32), parents=np.zeros((npar, 3), dtype=np.int32),
+               children=np.zeros((npar, 3 ** (dim - 1)), dtype=np.int32),
+               skeleton=np.zeros(nskel, dtype=np.int32),
+               send_off=np.zeros(nranks + 1, dtype=np.int64), send=np.zeros(nsend, dtype=np.int32),
+               recv_off=np.zeros(nranks + 1, dtype=np.int64), recv=np.zeros(nrecv, dtype=np.int32))
+    _check(None, lib().ader_mesh_subdomain(
+        mesh, _ptr(out["cuts"]), _ptr(out["ghosts"]), _ptr(out["conf"]), _ptr(out["parents"]),
+        _ptr(out["children"]), _ptr(out["skeleton"]), _ptr(out["send_off"]), _ptr(out["send"]),
+        _ptr(out["recv_off"]), _ptr(out["recv"])), "ader_mesh_subdomain")
+    return out

@@ -14,6 +14,7 @@ OUT = os.path.join(HERE, "libader.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_euler3d.cu", "k_euler2d.cu", "k_acoustics3d.cu", "k_acoustics2d.cu", "k_limiter3d.cu", "k_limiter2d.cu",
+           "partition.cpp",
            "k_common.cu", "k_noalloc.cu", "k_batch.cu", "api_batch.cpp", "k_adjoint.cu", "k_tc.cu", "api.cpp", "mesh.cpp", "basis.cpp"]
 
 

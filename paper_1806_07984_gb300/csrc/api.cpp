@@ -12,13 +12,28 @@
 #include "dispatch.h"
 #include "kernels.h"
 #include "mesh.h"
+#include "partition.h"
 
 using namespace ader;
 
 struct ader_ctx {
   ader_config cfg{};
   int n = 0, NS = 0, NF = 0, M = 0;
-  Tree tree;
+  Tree tree;                  // the whole mesh (every rank of a partition keeps it)
+  SubDomain dd;               // this rank's sub-domain once ader_partition ran
+  bool partitioned = false;
+  MeshLists* L = nullptr;     // lists the device step runs over: &tree or &dd.lists
+  // halo exchange lists of the partition on the device (all peers
+  // concatenated; host offsets per peer, in entries)
+  int32_t *halo_send = nullptr, *halo_recv = nullptr;
+  int64_t halo_send_cap = 0, halo_recv_cap = 0;
+  std::vector<int64_t> send_off, recv_off;
+  // state migration after a partitioned remesh: the transferred cells of the
+  // old base-cell range (tree cells [stage_first, stage_first + stage_count))
+  double* stage = nullptr;
+  int64_t stage_cap = 0, stage_first = 0, stage_count = 0;
+  std::vector<int64_t> old_base_cut;
+  bool migrating = false;
   BasisTables B{};
   double inv_h[kMaxLevels][3]{};
   cudaStream_t s_hi = nullptr, s_lo = nullptr;
@@ -200,17 +215,13 @@ void drop_step_graph(ader_ctx* c) {
 // Upload levels, cell lists and face lists of the current tree (synchronous).
 ader_status upload_mesh(ader_ctx* c) {
   drop_step_graph(c);
-  const Tree& t = c->tree;
-  const int64_t C = int64_t(t.cells.size());
+  const MeshLists& t = *c->L;
+  const int64_t C = t.nlocal;
   ader_status st = ensure_cells(c, C);
   if (st != ADER_OK) return st;
-  std::vector<int8_t> lv(static_cast<size_t>(C));
   std::vector<int32_t> all(static_cast<size_t>(C));
-  for (int64_t i = 0; i < C; ++i) {
-    lv[size_t(i)] = int8_t(t.cells[size_t(i)].level);
-    all[size_t(i)] = int32_t(i);
-  }
-  CK(cudaMemcpy(c->level, lv.data(), size_t(C), cudaMemcpyHostToDevice), "upload level");
+  for (int64_t i = 0; i < C; ++i) all[size_t(i)] = int32_t(i);
+  CK(cudaMemcpy(c->level, t.levels.data(), size_t(C), cudaMemcpyHostToDevice), "upload level");
   CK(cudaMemcpy(c->all_cells, all.data(), sizeof(int32_t) * size_t(C), cudaMemcpyHostToDevice),
      "upload cells");
   if (!t.skel_cells.empty())
@@ -240,6 +251,26 @@ ader_status upload_mesh(ader_ctx* c) {
     CK(cudaMemcpy(c->child_fine, t.child_fine.data(), sizeof(int32_t) * t.child_fine.size(),
                   cudaMemcpyHostToDevice), "upload children");
   }
+  if (c->partitioned) {
+    const SubDomain& dd = c->dd;
+    std::vector<int32_t> snd, rcv;
+    c->send_off.assign(size_t(dd.nranks) + 1, 0);
+    c->recv_off.assign(size_t(dd.nranks) + 1, 0);
+    for (int q = 0; q < dd.nranks; ++q) {
+      snd.insert(snd.end(), dd.send[size_t(q)].begin(), dd.send[size_t(q)].end());
+      rcv.insert(rcv.end(), dd.recv[size_t(q)].begin(), dd.recv[size_t(q)].end());
+      c->send_off[size_t(q) + 1] = int64_t(snd.size());
+      c->recv_off[size_t(q) + 1] = int64_t(rcv.size());
+    }
+    CK(grow(&c->halo_send, &c->halo_send_cap, std::max<int64_t>(int64_t(snd.size()), 1)), "cudaMalloc halo");
+    CK(grow(&c->halo_recv, &c->halo_recv_cap, std::max<int64_t>(int64_t(rcv.size()), 1)), "cudaMalloc halo");
+    if (!snd.empty())
+      CK(cudaMemcpy(c->halo_send, snd.data(), sizeof(int32_t) * snd.size(), cudaMemcpyHostToDevice),
+         "upload halo");
+    if (!rcv.empty())
+      CK(cudaMemcpy(c->halo_recv, rcv.data(), sizeof(int32_t) * rcv.size(), cudaMemcpyHostToDevice),
+         "upload halo");
+  }
   if (c->cfg.limiter) {
     // conforming neighbour across each face, -1 across a resolution transition
     const int F = 2 * c->cfg.dim;
@@ -266,13 +297,13 @@ PredictArgs predict_args(ader_ctx* c, const double* dt, ader_set set) {
   a.faceF = c->faceF;
   if (set == ADER_SKELETON) {
     a.cells = c->skel_cells;
-    a.count = int64_t(c->tree.skel_cells.size());
+    a.count = int64_t(c->L->skel_cells.size());
   } else if (set == ADER_ENCLAVE) {
     a.cells = c->encl_cells;
-    a.count = int64_t(c->tree.encl_cells.size());
+    a.count = int64_t(c->L->encl_cells.size());
   } else {
     a.cells = c->all_cells;
-    a.count = int64_t(c->tree.cells.size());
+    a.count = c->L->nowned;
   }
   a.level = c->level;
   a.dt = dt;
@@ -291,7 +322,7 @@ RiemannArgs riemann_args(ader_ctx* c) {
   a.fstar = c->fstar;
   a.parents = c->parents;
   a.child_fine = c->child_fine;
-  a.nparents = int64_t(c->tree.parents.size());
+  a.nparents = int64_t(c->L->parents.size());
   a.gamma = c->cfg.gamma;
   a.status = stage_status(c);
   a.B = c->B;
@@ -304,7 +335,7 @@ CorrectArgs correct_args(ader_ctx* c, const double* dt) {
   a.fstar = c->fstar;
   a.u = c->u;
   a.level = c->level;
-  a.ncells = int64_t(c->tree.cells.size());
+  a.ncells = c->L->nowned;
   a.dt = dt;
   a.rate_max = c->rate;
   a.gamma = c->cfg.gamma;
@@ -316,7 +347,7 @@ CorrectArgs correct_args(ader_ctx* c, const double* dt) {
 
 ader_status enqueue_riemann(ader_ctx* c, ader_set set, cudaStream_t s) {
   RiemannArgs a = riemann_args(c);
-  const Tree& t = c->tree;
+  const MeshLists& t = *c->L;
   if (set == ADER_ALL || set == ADER_SKELETON) {
     CK(do_faces(c, 1, a, s), "riemann child faces");
     CK(do_faces(c, 2, a, s), "restriction");
@@ -351,7 +382,7 @@ LimiterArgs limiter_args(ader_ctx* c, const double* dt) {
   a.fix_list = c->fix_list;
   a.counts = c->lim_counts;
   a.level = c->level;
-  a.ncells = int64_t(c->tree.cells.size());
+  a.ncells = c->L->nowned;
   a.dt = dt;
   a.gamma = c->cfg.gamma;
   a.delta0 = c->cfg.limiter_delta0 > 0.0 ? c->cfg.limiter_delta0 : 1e-4;
@@ -419,6 +450,18 @@ ader_status enqueue_correct(ader_ctx* c, const double* dt, double* dt_next, cuda
   }
   CK(do_correct(c, true, stage_correct_args(c, dt, nullptr, 0), s), "corrector");
   return enqueue_finish(c, dt, dt_next, s);
+}
+
+// This rank's sub-domain for the tree's current mesh under base_cut, uploaded.
+ader_status rebuild_subdomain(ader_ctx* c, const std::vector<int64_t>& base_cut) {
+  std::vector<int64_t> starts;
+  if (!base_starts(c->tree, &starts)) {
+    c->err = "the cell order does not follow the base cells";
+    return ADER_ERR_MESH;
+  }
+  build_subdomain(c->tree, starts, base_cut, c->dd.rank, &c->dd);
+  c->L = &c->dd.lists;
+  return upload_mesh(c);
 }
 
 bool valid_config(const ader_config* cfg, std::string* why) {
@@ -497,6 +540,7 @@ ader_status ader_init(const ader_config* cfg, ader_ctx** out) {
                                           (c->cfg.hi[d] - c->cfg.lo[d])
                                     : 0.0;
   c->tree = Tree(cfg->dim, c->cfg.base, cfg->max_level);
+  c->L = &c->tree;
   if (!c->tree.build()) {
     delete c;
     return ADER_ERR_MESH;
@@ -542,7 +586,7 @@ ader_status ader_init(const ader_config* cfg, ader_ctx** out) {
   st = upload_mesh(c);
   if (st != ADER_OK) return fail(st);
   const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
-  if (cudaMemset(c->u, 0, cell_bytes * c->tree.cells.size()) != cudaSuccess) return fail(ADER_ERR_CUDA);
+  if (cudaMemset(c->u, 0, cell_bytes * size_t(c->L->nlocal)) != cudaSuccess) return fail(ADER_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(ADER_ERR_CUDA);
   *out = c;
   return ADER_OK;
@@ -560,7 +604,8 @@ void ader_destroy(ader_ctx* c) {
                   (void*)c->lim_flags, (void*)c->lim_list, (void*)c->fix_list, (void*)c->nbr,
                   (void*)c->force, (void*)c->lim_counts, (void*)c->rate_cand,
                   (void*)c->status_cand, (void*)c->corr_cells, (void*)c->plan_dev,
-                  (void*)c->kids_dev, (void*)c->fv_scratch})
+                  (void*)c->kids_dev, (void*)c->fv_scratch, (void*)c->halo_send,
+                  (void*)c->halo_recv, (void*)c->stage})
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev_chunk)
     if (e) cudaEventDestroy(e);
@@ -574,17 +619,18 @@ void ader_destroy(ader_ctx* c) {
 ader_status ader_mesh_info(ader_ctx* c, int64_t* ncells, int64_t* nskel, int64_t* nconf,
                            int64_t* nparents) {
   if (!c) return ADER_ERR_ARG;
-  if (ncells) *ncells = int64_t(c->tree.cells.size());
-  if (nskel) *nskel = int64_t(c->tree.skel_cells.size());
-  if (nconf) *nconf = int64_t(c->tree.conf.size());
-  if (nparents) *nparents = int64_t(c->tree.parents.size());
+  if (ncells) *ncells = c->L->nowned;
+  if (nskel) *nskel = int64_t(c->L->skel_cells.size());
+  if (nconf) *nconf = int64_t(c->L->conf.size());
+  if (nparents) *nparents = int64_t(c->L->parents.size());
   return ADER_OK;
 }
 
 ader_status ader_mesh_cells(ader_ctx* c, int32_t* out) {
   if (!c || !out) return ADER_ERR_ARG;
-  for (size_t i = 0; i < c->tree.cells.size(); ++i) {
-    const Key& k = c->tree.cells[i];
+  const size_t first = c->partitioned ? size_t(c->dd.first) : 0;
+  for (size_t i = 0; i < size_t(c->L->nowned); ++i) {
+    const Key& k = c->tree.cells[first + i];
     out[4 * i + 0] = k.level;
     out[4 * i + 1] = k.x[0];
     out[4 * i + 2] = k.x[1];
@@ -595,7 +641,8 @@ ader_status ader_mesh_cells(ader_ctx* c, int32_t* out) {
 
 ader_status ader_mesh_skeleton(ader_ctx* c, uint8_t* out) {
   if (!c || !out) return ADER_ERR_ARG;
-  std::memcpy(out, c->tree.skeleton.data(), c->tree.skeleton.size());
+  std::memset(out, 0, size_t(c->L->nowned));
+  for (int32_t i : c->L->skel_cells) out[i] = 1;
   return ADER_OK;
 }
 
@@ -617,21 +664,20 @@ static ader_status copy_cells(ader_ctx* c, double* dst, const double* src, size_
 
 ader_status ader_set_state(ader_ctx* c, const double* u, int on_device, void* stream) {
   if (!c || !u) return ADER_ERR_ARG;
-  const size_t bytes = size_t(c->M) * c->NS * sizeof(double) * c->tree.cells.size();
+  const size_t bytes = size_t(c->M) * c->NS * sizeof(double) * size_t(c->L->nowned);
   return copy_cells(c, c->u, u, bytes, on_device, true, stream);
 }
 
 ader_status ader_get_state(ader_ctx* c, double* u, int on_device, void* stream) {
   if (!c || !u) return ADER_ERR_ARG;
-  const size_t bytes = size_t(c->M) * c->NS * sizeof(double) * c->tree.cells.size();
+  const size_t bytes = size_t(c->M) * c->NS * sizeof(double) * size_t(c->L->nowned);
   return copy_cells(c, u, c->u, bytes, on_device, false, stream);
 }
 
 ader_status ader_get_field(ader_ctx* c, ader_field f, double* out, int on_device, void* stream) {
   if (!c || !out) return ADER_ERR_ARG;
-  const size_t C = c->tree.cells.size();
-  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double) * C;
-  const size_t face_bytes = size_t(2 * c->cfg.dim) * c->M * c->NF * sizeof(double) * C;
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double) * size_t(c->L->nowned);
+  const size_t face_bytes = size_t(2 * c->cfg.dim) * c->M * c->NF * sizeof(double) * size_t(c->L->nlocal);
   switch (f) {
     case ADER_FIELD_U: return copy_cells(c, out, c->u, cell_bytes, on_device, false, stream);
     case ADER_FIELD_USTAR: return copy_cells(c, out, c->ustar, cell_bytes, on_device, false, stream);
@@ -673,7 +719,7 @@ ader_status ader_correct(ader_ctx* c, const double* dt_dev, double* dt_next_dev,
 // high-priority stream solves the faces completed by it and corrects the
 // cells whose faces are then all solved (Tree::set_chunks).
 ader_status step_pipelined(ader_ctx* c, double* dt_dev) {
-  const Tree& t = c->tree;
+  const MeshLists& t = *c->L;
   const int K = t.chunks;
   while (int(c->ev_chunk.size()) < K) {
     cudaEvent_t e = nullptr;
@@ -725,7 +771,7 @@ ader_status step_pipelined(ader_ctx* c, double* dt_dev) {
 
 // One step's work on s_hi / s_lo (joined back into s_hi at the end).
 ader_status enqueue_step(ader_ctx* c, double* dt_dev) {
-  if (c->tree.chunks > 1) return step_pipelined(c, dt_dev);
+  if (c->L->chunks > 1) return step_pipelined(c, dt_dev);
   CK(cudaEventRecord(c->ev_step, c->s_hi), "event");
   CK(cudaStreamWaitEvent(c->s_lo, c->ev_step, 0), "event");
   PredictArgs ps = predict_args(c, dt_dev, ADER_SKELETON);
@@ -769,6 +815,11 @@ void capture_step(ader_ctx* c, double* dt_dev) {
 
 ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
   if (!c || !dt_dev || nsteps < 0) return ADER_ERR_ARG;
+  if (c->partitioned) {
+    c->err = "a partitioned context steps by ader_predict, ader_halo_pack/unpack, ader_riemann "
+             "and ader_correct, with the exchange between them";
+    return ADER_ERR_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaEventRecord(c->ev_begin, s), "event");
   CK(cudaStreamWaitEvent(c->s_hi, c->ev_begin, 0), "event");
@@ -784,7 +835,7 @@ ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
     }
   }
   for (int k = 0; k < nsteps; ++k) {
-    if (c->tree.chunks > 1) {
+    if (c->L->chunks > 1) {
       ader_status st = step_pipelined(c, dt_dev);
       if (st != ADER_OK) return st;
       continue;
@@ -814,12 +865,122 @@ ader_status ader_classify(ader_ctx* c, const int8_t* flags) {
   if (!c) return ADER_ERR_ARG;
   CK(cudaDeviceSynchronize(), "sync before classify");
   c->tree.classify(flags);
+  if (c->partitioned) return rebuild_subdomain(c, c->dd.base_cut);
   return upload_mesh(c);
 }
+
+namespace {
+
+// Partitioned remesh: every rank adapts its copy of the whole tree with the
+// same flags; the cells of the rank's old base-cell range get their data from
+// its old owned cells (no family crosses a cut), into the staging buffer;
+// then the cuts are rebalanced and the overlap of the staging range with the
+// new owned range is copied into u.  The rest arrives by ader_migrate_unpack.
+ader_status remesh_partitioned(ader_ctx* c, const int8_t* flags) {
+  const std::vector<int64_t> old_cut = c->dd.base_cut;
+  const int64_t o0 = c->dd.first, nold = c->L->nowned;
+  const int R = c->dd.nranks, r = c->dd.rank;
+  std::vector<TransferItem> plan;
+  std::vector<int32_t> kids;
+  if (!c->tree.remesh(flags, &plan, &kids)) {
+    c->err = c->tree.error();
+    return ADER_ERR_MESH;
+  }
+  c->force_set = false;
+  std::vector<int64_t> starts;
+  if (!base_starts(c->tree, &starts)) {
+    c->err = "the cell order does not follow the base cells";
+    return ADER_ERR_MESH;
+  }
+  const int64_t n0 = starts[size_t(old_cut[size_t(r)])], n1 = starts[size_t(old_cut[size_t(r) + 1])];
+  const int S = int(ipow64(3, c->cfg.dim));
+  std::vector<TransferItem> lplan(size_t(n1 - n0));
+  std::vector<int32_t> lkids;
+  for (int64_t g = n0; g < n1; ++g) {
+    TransferItem it = plan[size_t(g)];
+    if (it.kind == 2) {
+      const int32_t off = int32_t(lkids.size());
+      for (int j = 0; j < S; ++j) {
+        const int64_t k = int64_t(kids[size_t(it.src) + size_t(j)]) - o0;
+        if (k < 0 || k >= nold) {
+          c->err = "a coarsened family crosses a partition cut";
+          return ADER_ERR_MESH;
+        }
+        lkids.push_back(int32_t(k));
+      }
+      it.src = off;
+    } else {
+      it.src = int32_t(int64_t(it.src) - o0);
+      if (it.src < 0 || it.src >= nold) {
+        c->err = "a new cell takes data from another partition";
+        return ADER_ERR_MESH;
+      }
+    }
+    lplan[size_t(g - n0)] = it;
+  }
+  const int64_t cell_doubles = int64_t(c->M) * c->NS;
+  CK(grow(&c->stage, &c->stage_cap, std::max<int64_t>(n1 - n0, 1) * cell_doubles), "cudaMalloc staging");
+  CK(grow(&c->plan_dev, &c->plan_cap, std::max<int64_t>(int64_t(lplan.size()), 1)), "cudaMalloc plan");
+  CK(grow(&c->kids_dev, &c->kids_cap, std::max<int64_t>(int64_t(lkids.size()), 1)), "cudaMalloc kids");
+  if (!lplan.empty())
+    CK(cudaMemcpy(c->plan_dev, lplan.data(), sizeof(TransferItem) * lplan.size(), cudaMemcpyHostToDevice),
+       "upload plan");
+  if (!lkids.empty())
+    CK(cudaMemcpy(c->kids_dev, lkids.data(), sizeof(int32_t) * lkids.size(), cudaMemcpyHostToDevice),
+       "upload kids");
+  TransferArgs a{};
+  a.u_old = c->u;
+  a.u_new = c->stage;
+  a.plan = c->plan_dev;
+  a.children = c->kids_dev;
+  a.ncells_new = n1 - n0;
+  a.ncells_old = nold;
+  a.status = c->status;
+  a.B = c->B;
+  CK(do_transfer(c, a, nullptr), "transfer");
+  CK(cudaDeviceSynchronize(), "transfer sync");
+  std::vector<int64_t> base_cut;
+  if (!balanced_cuts(starts, R, &base_cut)) {
+    c->err = "more ranks than base cells";
+    return ADER_ERR_MESH;
+  }
+  c->old_base_cut = old_cut;
+  c->stage_first = n0;
+  c->stage_count = n1 - n0;
+  ader_status st = rebuild_subdomain(c, base_cut);
+  if (st != ADER_OK) return st;
+  const int64_t m0 = c->dd.first, m1 = m0 + c->L->nowned;
+  const int64_t lo = std::max(n0, m0), hi = std::min(n1, m1);
+  if (hi > lo)
+    CK(cudaMemcpy(c->u + (lo - m0) * cell_doubles, c->stage + (lo - n0) * cell_doubles,
+                  sizeof(double) * size_t((hi - lo) * cell_doubles), cudaMemcpyDeviceToDevice),
+       "keep own cells");
+  c->migrating = true;
+  return ADER_OK;
+}
+
+// Tree cells [lo, hi) that this rank sends to `peer` (send) or receives from
+// it (recv) after a partitioned remesh.
+void migration_range(const ader_ctx* c, int peer, bool send, int64_t* lo, int64_t* hi) {
+  std::vector<int64_t> starts;
+  *lo = *hi = 0;
+  if (!c->migrating || !base_starts(c->tree, &starts)) return;
+  const std::vector<int64_t>& oc = c->old_base_cut;
+  const std::vector<int64_t>& nc = c->dd.base_cut;
+  const int me = c->dd.rank;
+  const int src = send ? me : peer, dst = send ? peer : me;
+  const int64_t a0 = starts[size_t(oc[size_t(src)])], a1 = starts[size_t(oc[size_t(src) + 1])];
+  const int64_t b0 = starts[size_t(nc[size_t(dst)])], b1 = starts[size_t(nc[size_t(dst) + 1])];
+  *lo = std::max(a0, b0);
+  *hi = std::max(*lo, std::min(a1, b1));
+}
+
+}  // namespace
 
 ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   if (!c || !flags) return ADER_ERR_ARG;
   CK(cudaDeviceSynchronize(), "sync before remesh");
+  if (c->partitioned) return remesh_partitioned(c, flags);
   const int64_t C_old = int64_t(c->tree.cells.size());
   std::vector<TransferItem> plan;
   std::vector<int32_t> kids;
@@ -874,7 +1035,7 @@ cudaError_t enqueue_indicator(ader_ctx* c, int var, int deriv, double* eta, cuda
   IndicatorArgs a{};
   a.u = c->u;
   a.level = c->level;
-  a.ncells = int64_t(c->tree.cells.size());
+  a.ncells = c->L->nowned;
   a.var = var;
   a.deriv = deriv;
   a.eta = eta;
@@ -891,7 +1052,7 @@ cudaError_t enqueue_indicator(ader_ctx* c, int var, int deriv, double* eta, cuda
 
 ader_status ader_gradient_indicator(ader_ctx* c, int var, int deriv, double* eta_dev, void* stream) {
   if (!c || var < 0 || var >= c->M || (deriv != 1 && deriv != 2)) return ADER_ERR_ARG;
-  if (!eta_dev && !c->tree.cells.empty()) return ADER_ERR_ARG;
+  if (!eta_dev && c->L->nowned > 0) return ADER_ERR_ARG;
   CK(enqueue_indicator(c, var, deriv, eta_dev, static_cast<cudaStream_t>(stream)), "gradient indicator");
   return ADER_OK;
 }
@@ -901,7 +1062,7 @@ ader_status ader_gradient_flags(ader_ctx* c, int var, int deriv, double refine_a
   if (!c || !flags || var < 0 || var >= c->M || (deriv != 1 && deriv != 2) ||
       !(refine_above >= coarsen_below))
     return ADER_ERR_ARG;
-  const int64_t C = int64_t(c->tree.cells.size());
+  const int64_t C = c->L->nowned;
   // the state may still be written by steps on the caller's (non-blocking) streams
   CK(cudaDeviceSynchronize(), "sync before gradient indicator");
   double* d_eta = nullptr;
@@ -914,7 +1075,7 @@ ader_status ader_gradient_flags(ader_ctx* c, int var, int deriv, double refine_a
   cudaFree(d_eta);
   if (e != cudaSuccess) return cuda_fail(c, e, "gradient indicator");
   for (int64_t i = 0; i < C; ++i) {
-    const int lv = c->tree.cells[size_t(i)].level;
+    const int lv = c->L->levels[size_t(i)];
     int8_t f = 0;
     if (eta[size_t(i)] > refine_above && lv < c->cfg.max_level)
       f = 1;
@@ -947,8 +1108,8 @@ ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out
     c->err = "the adjoint step is implemented for linear acoustics in FP64";
     return ADER_ERR_ARG;
   }
-  if (!c->tree.parents.empty()) {
-    c->err = "the adjoint step needs a mesh without resolution transitions";
+  if (!c->tree.parents.empty() || c->partitioned) {
+    c->err = "the adjoint step needs an unpartitioned mesh without resolution transitions";
     return ADER_ERR_ARG;
   }
   AdjointArgs a{};
@@ -1042,8 +1203,135 @@ ader_status ader_launch_count(ader_ctx* c, int64_t* out) {
   return ADER_OK;
 }
 
+ader_status ader_partition(ader_ctx* c, int nranks, int rank) {
+  if (!c || nranks < 1 || rank < 0 || rank >= nranks) return ADER_ERR_ARG;
+  if (c->partitioned) {
+    c->err = "the context is partitioned already";
+    return ADER_ERR_ARG;
+  }
+  if (nranks == 1) return ADER_OK;
+  if (c->cfg.limiter) {
+    c->err = "the subcell limiter needs neighbour states: not available on a partition";
+    return ADER_ERR_ARG;
+  }
+  CK(cudaDeviceSynchronize(), "sync before partition");
+  std::vector<int64_t> starts, base_cut;
+  if (!base_starts(c->tree, &starts)) {
+    c->err = "the cell order does not follow the base cells";
+    return ADER_ERR_MESH;
+  }
+  if (!balanced_cuts(starts, nranks, &base_cut)) {
+    c->err = "more ranks than base cells";
+    return ADER_ERR_ARG;
+  }
+  // keep the owned rows of the state, moved to the front (u* is free
+  // between steps and has the same capacity)
+  const int64_t g0 = starts[size_t(base_cut[size_t(rank)])];
+  const int64_t g1 = starts[size_t(base_cut[size_t(rank) + 1])];
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
+  if (g1 > g0)
+    CK(cudaMemcpy(c->ustar, c->u + g0 * int64_t(c->M) * c->NS, cell_bytes * size_t(g1 - g0),
+                  cudaMemcpyDeviceToDevice), "keep owned state");
+  std::swap(c->u, c->ustar);
+  c->dd.rank = rank;
+  c->dd.nranks = nranks;
+  c->partitioned = true;
+  c->migrating = false;
+  return rebuild_subdomain(c, base_cut);
+}
+
+ader_status ader_dd_info(ader_ctx* c, int* nranks, int* rank, int64_t* nglobal, int64_t* first,
+                         int64_t* nowned, int64_t* nghost) {
+  if (!c) return ADER_ERR_ARG;
+  if (nranks) *nranks = c->partitioned ? c->dd.nranks : 1;
+  if (rank) *rank = c->partitioned ? c->dd.rank : 0;
+  if (nglobal) *nglobal = int64_t(c->tree.cells.size());
+  if (first) *first = c->partitioned ? c->dd.first : 0;
+  if (nowned) *nowned = c->L->nowned;
+  if (nghost) *nghost = c->L->nlocal - c->L->nowned;
+  return ADER_OK;
+}
+
+ader_status ader_dd_cuts(ader_ctx* c, int64_t* cuts) {
+  if (!c || !cuts) return ADER_ERR_ARG;
+  if (!c->partitioned) {
+    cuts[0] = 0;
+    cuts[1] = int64_t(c->tree.cells.size());
+    return ADER_OK;
+  }
+  std::copy(c->dd.cut.begin(), c->dd.cut.end(), cuts);
+  return ADER_OK;
+}
+
+ader_status ader_halo_size(ader_ctx* c, int peer, int64_t* send_doubles, int64_t* recv_doubles) {
+  if (!c || !c->partitioned || peer < 0 || peer >= c->dd.nranks) return ADER_ERR_ARG;
+  const int64_t blk = 2 * int64_t(c->M) * c->NF;
+  if (send_doubles) *send_doubles = blk * int64_t(c->dd.send[size_t(peer)].size());
+  if (recv_doubles) *recv_doubles = blk * int64_t(c->dd.recv[size_t(peer)].size());
+  return ADER_OK;
+}
+
+ader_status ader_halo_pack(ader_ctx* c, int peer, double* buf_dev, void* stream) {
+  if (!c || !c->partitioned || peer < 0 || peer >= c->dd.nranks) return ADER_ERR_ARG;
+  const int64_t b = c->send_off[size_t(peer)], e = c->send_off[size_t(peer) + 1];
+  if (e == b) return ADER_OK;
+  if (!buf_dev) return ADER_ERR_ARG;
+  c->launches += 1;
+  CK(launch_halo_pack(c->faceQ, c->faceF, c->halo_send + b, e - b, c->M * c->NF, buf_dev,
+                      static_cast<cudaStream_t>(stream)), "halo pack");
+  return ADER_OK;
+}
+
+ader_status ader_halo_unpack(ader_ctx* c, int peer, const double* buf_dev, void* stream) {
+  if (!c || !c->partitioned || peer < 0 || peer >= c->dd.nranks) return ADER_ERR_ARG;
+  const int64_t b = c->recv_off[size_t(peer)], e = c->recv_off[size_t(peer) + 1];
+  if (e == b) return ADER_OK;
+  if (!buf_dev) return ADER_ERR_ARG;
+  c->launches += 1;
+  CK(launch_halo_unpack(c->faceQ, c->faceF, c->halo_recv + b, e - b, c->M * c->NF, buf_dev,
+                        static_cast<cudaStream_t>(stream)), "halo unpack");
+  return ADER_OK;
+}
+
+ader_status ader_migrate_size(ader_ctx* c, int peer, int64_t* send_doubles, int64_t* recv_doubles) {
+  if (!c || !c->partitioned || peer < 0 || peer >= c->dd.nranks) return ADER_ERR_ARG;
+  int64_t lo, hi;
+  const int64_t cd = int64_t(c->M) * c->NS;
+  migration_range(c, peer, true, &lo, &hi);
+  if (send_doubles) *send_doubles = peer == c->dd.rank ? 0 : (hi - lo) * cd;
+  migration_range(c, peer, false, &lo, &hi);
+  if (recv_doubles) *recv_doubles = peer == c->dd.rank ? 0 : (hi - lo) * cd;
+  return ADER_OK;
+}
+
+ader_status ader_migrate_pack(ader_ctx* c, int peer, double* buf_dev, void* stream) {
+  if (!c || !c->partitioned || peer < 0 || peer >= c->dd.nranks) return ADER_ERR_ARG;
+  int64_t lo, hi;
+  migration_range(c, peer, true, &lo, &hi);
+  if (hi == lo || peer == c->dd.rank) return ADER_OK;
+  if (!buf_dev) return ADER_ERR_ARG;
+  const int64_t cd = int64_t(c->M) * c->NS;
+  CK(cudaMemcpyAsync(buf_dev, c->stage + (lo - c->stage_first) * cd, sizeof(double) * size_t((hi - lo) * cd),
+                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)), "migrate pack");
+  return ADER_OK;
+}
+
+ader_status ader_migrate_unpack(ader_ctx* c, int peer, const double* buf_dev, void* stream) {
+  if (!c || !c->partitioned || peer < 0 || peer >= c->dd.nranks) return ADER_ERR_ARG;
+  int64_t lo, hi;
+  migration_range(c, peer, false, &lo, &hi);
+  if (hi == lo || peer == c->dd.rank) return ADER_OK;
+  if (!buf_dev) return ADER_ERR_ARG;
+  const int64_t cd = int64_t(c->M) * c->NS;
+  CK(cudaMemcpyAsync(c->u + (lo - c->dd.first) * cd, buf_dev, sizeof(double) * size_t((hi - lo) * cd),
+                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)), "migrate unpack");
+  return ADER_OK;
+}
+
 struct ader_mesh {
   Tree tree;
+  SubDomain dd;
+  bool has_dd = false;
 };
 
 ader_status ader_mesh_create(int dim, const int base[3], int max_level, ader_mesh** out) {
@@ -1069,6 +1357,7 @@ void ader_mesh_destroy(ader_mesh* m) { delete m; }
 
 ader_status ader_mesh_adapt(ader_mesh* m, const int8_t* flags) {
   if (!m || !flags) return ADER_ERR_ARG;
+  m->has_dd = false;
   std::vector<TransferItem> plan;
   std::vector<int32_t> kids;
   return m->tree.remesh(flags, &plan, &kids) ? ADER_OK : ADER_ERR_MESH;
@@ -1127,6 +1416,63 @@ ader_status ader_mesh_sphere_flags(ader_mesh* m, const double center[3], double 
 ader_status ader_mesh_refine_around(ader_mesh* m, const uint8_t* troubled, int8_t* flags) {
   if (!m || !troubled || !flags) return ADER_ERR_ARG;
   m->tree.refine_around(troubled, flags);
+  return ADER_OK;
+}
+
+ader_status ader_mesh_partition(ader_mesh* m, int nranks, int rank, int64_t* sizes) {
+  if (!m || nranks < 1 || rank < 0 || rank >= nranks || !sizes) return ADER_ERR_ARG;
+  std::vector<int64_t> starts, base_cut;
+  if (!base_starts(m->tree, &starts)) return ADER_ERR_MESH;
+  if (!balanced_cuts(starts, nranks, &base_cut)) return ADER_ERR_ARG;
+  m->dd.rank = rank;
+  build_subdomain(m->tree, starts, base_cut, rank, &m->dd);
+  m->has_dd = true;
+  const MeshLists& L = m->dd.lists;
+  int64_t ns = 0, nr = 0;
+  for (int q = 0; q < nranks; ++q) {
+    ns += int64_t(m->dd.send[size_t(q)].size());
+    nr += int64_t(m->dd.recv[size_t(q)].size());
+  }
+  const int64_t v[9] = {m->dd.first, L.nowned, L.nlocal - L.nowned, int64_t(L.conf.size()),
+                        L.n_conf_skeleton, int64_t(L.parents.size()), int64_t(L.skel_cells.size()), ns, nr};
+  std::copy(v, v + 9, sizes);
+  return ADER_OK;
+}
+
+ader_status ader_mesh_subdomain(ader_mesh* m, int64_t* cuts, int32_t* ghosts, int32_t* conf_out,
+                                int32_t* parents_out, int32_t* child_out, int32_t* skel_out,
+                                int64_t* send_off, int32_t* send_out, int64_t* recv_off,
+                                int32_t* recv_out) {
+  if (!m || !m->has_dd) return ADER_ERR_ARG;
+  const SubDomain& dd = m->dd;
+  const MeshLists& L = dd.lists;
+  if (cuts) std::copy(dd.cut.begin(), dd.cut.end(), cuts);
+  if (ghosts) std::copy(dd.ghosts.begin(), dd.ghosts.end(), ghosts);
+  if (conf_out)
+    for (size_t i = 0; i < L.conf.size(); ++i) {
+      conf_out[3 * i + 0] = L.conf[i].left;
+      conf_out[3 * i + 1] = L.conf[i].right;
+      conf_out[3 * i + 2] = L.conf[i].dir;
+    }
+  if (parents_out)
+    for (size_t i = 0; i < L.parents.size(); ++i) {
+      parents_out[3 * i + 0] = L.parents[i].coarse;
+      parents_out[3 * i + 1] = L.parents[i].dir;
+      parents_out[3 * i + 2] = L.parents[i].coarse_side;
+    }
+  if (child_out) std::copy(L.child_fine.begin(), L.child_fine.end(), child_out);
+  if (skel_out) std::copy(L.skel_cells.begin(), L.skel_cells.end(), skel_out);
+  int64_t ps = 0, pr = 0;
+  for (int q = 0; q < dd.nranks; ++q) {
+    if (send_off) send_off[q] = ps;
+    if (recv_off) recv_off[q] = pr;
+    if (send_out) std::copy(dd.send[size_t(q)].begin(), dd.send[size_t(q)].end(), send_out + ps);
+    if (recv_out) std::copy(dd.recv[size_t(q)].begin(), dd.recv[size_t(q)].end(), recv_out + pr);
+    ps += int64_t(dd.send[size_t(q)].size());
+    pr += int64_t(dd.recv[size_t(q)].size());
+  }
+  if (send_off) send_off[dd.nranks] = ps;
+  if (recv_off) recv_off[dd.nranks] = pr;
   return ADER_OK;
 }
 

@@ -176,6 +176,12 @@ cudaError_t launch_rate(int dim, int order, int pde, const CorrectArgs& a, cudaS
 cudaError_t launch_finalize_dt(unsigned long long* rate_max, double cfl, double* dt_next,
                                uint32_t* status, cudaStream_t s);
 cudaError_t launch_transfer(int dim, int order, int nvar, const TransferArgs& a, cudaStream_t s);
+// Halo exchange of a partitioned mesh: gather / scatter `count` face slots
+// (local cell * 2d + slot) of Q-bar and F-bar, blk = M NF values each.
+cudaError_t launch_halo_pack(const double* faceQ, const double* faceF, const int32_t* slots,
+                             int64_t count, int blk, double* buf, cudaStream_t s);
+cudaError_t launch_halo_unpack(double* faceQ, double* faceF, const int32_t* slots, int64_t count,
+                               int blk, const double* buf, cudaStream_t s);
 
 struct AdjointArgs {
   const double* lam_in;   // lambda for u(T+dt)      [c][var][node]

@@ -247,6 +247,9 @@ bool Tree::build() {
     child_fine.insert(child_fine.end(), P.child_fine.begin(), P.child_fine.end());
     for (int32_t c : P.marked) transition[size_t(c)] = 1;
   }
+  nlocal = nowned = n;
+  levels.resize(size_t(n));
+  for (int64_t i = 0; i < n; ++i) levels[size_t(i)] = int8_t(cells[size_t(i)].level);
   classify(nullptr);
   error_.clear();
   return true;

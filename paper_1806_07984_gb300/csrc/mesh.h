@@ -128,41 +128,55 @@ struct TransferItem {
   int32_t pad;
 };
 
-class Tree {
+// The lists a device step launches over, in one cell numbering: the whole
+// mesh (Tree) or one sub-domain of a partition (SubDomain).  Cells
+// [0, nowned) are predicted and corrected; cells [nowned, nlocal) are ghosts
+// whose face data arrive by exchange (none outside a partition).
+struct MeshLists {
+  int64_t nlocal = 0, nowned = 0;
+  std::vector<int8_t> levels;             // per local cell
+
+  // Skeleton/enclave split: skel_cells + encl_cells partition [0, nowned).
+  // conf: the conforming faces, those whose two cells are both skeleton
+  // first (n_conf_skeleton of them).
+  std::vector<int32_t> skel_cells, encl_cells;
+  std::vector<ConfFace> conf;
+  int64_t n_conf_skeleton = 0;
+  std::vector<ParentFace> parents;
+  std::vector<int32_t> child_fine;
+
+  // Enclave pipeline of a step (Tree::set_chunks(K), recomputed by
+  // classify()): the enclave cells split into K contiguous chunks
+  // encl_cells[chunk_off[k] .. chunk_off[k+1]); the conforming faces after
+  // the skeleton ones ordered by the chunk whose predictor completes their two
+  // cells, conf[n_conf_skeleton + face_off[k] .. n_conf_skeleton +
+  // face_off[k+1]); and every cell in corr_cells, grouped by the stage after
+  // which all its face fluxes exist: group 0 after the skeleton tasks, group
+  // k + 1 after chunk k (corr_cells[corr_off[g] .. corr_off[g+1])).
+  int chunks = 1;
+  std::vector<int64_t> chunk_off, face_off, corr_off;
+  std::vector<int32_t> corr_cells;
+};
+
+class Tree : public MeshLists {
  public:
   Tree() = default;
   Tree(int dim, const int base[3], int max_level);
 
   int dim() const { return dim_; }
   int max_level() const { return max_level_; }
+  const int* base() const { return base_; }
   int64_t dims(int level, int d) const;
 
   // The ordered cell list and its derived structures.  Rebuilt by build().
   std::vector<Key> cells;
   std::vector<uint8_t> transition;        // per cell: touches a resolution transition
   std::vector<ConfFace> conf_all;         // conforming faces, build order
-  std::vector<ParentFace> parents;
-  std::vector<int32_t> child_fine;
 
   // Skeleton/enclave split (classify()): skeleton = transition cells plus
-  // cells flagged for refinement.  conf is conf_all with the faces whose two
-  // cells are both skeleton first (n_conf_skeleton of them).
+  // cells flagged for refinement.  conf (MeshLists) is conf_all with the
+  // faces whose two cells are both skeleton first.
   std::vector<uint8_t> skeleton;
-  std::vector<int32_t> skel_cells, encl_cells;
-  std::vector<ConfFace> conf;
-  int64_t n_conf_skeleton = 0;
-
-  // Enclave pipeline of a step (set_chunks(K), recomputed by classify()):
-  // the enclave cells split into K contiguous chunks encl_cells[chunk_off[k] ..
-  // chunk_off[k+1]); the conforming faces after the skeleton ones ordered by the
-  // chunk whose predictor completes their two cells, conf[n_conf_skeleton +
-  // face_off[k] .. n_conf_skeleton + face_off[k+1]); and every cell in
-  // corr_cells, grouped by the stage after which all its face fluxes exist:
-  // group 0 after the skeleton tasks, group k + 1 after chunk k
-  // (corr_cells[corr_off[g] .. corr_off[g+1])).
-  int chunks = 1;
-  std::vector<int64_t> chunk_off, face_off, corr_off;
-  std::vector<int32_t> corr_cells;
   void set_chunks(int K);
 
   // Rebuild order and faces.  Returns false and sets error() if the mesh is
