@@ -14,8 +14,10 @@ prolongation, Riemann, restriction, corrector, CFL reduction; the remesh of
 every 10th step is inside the timed region).
 
 Metric: DoF-updates/s = sum over cells of m n^3, times steps, over time.
-Multi-GPU runs (torchrun) are independent replicas, one per rank (weak
-scaling); the value sums all ranks' DoF-updates over the slowest rank's time.
+Multi-GPU runs (torchrun) partition the one mesh along its depth-first cell
+order (strong scaling): each rank steps its sub-domain and exchanges the
+partition-face data every step; the value sums all ranks' owned DoF-updates
+over the slowest rank's time.
 """
 import argparse
 import json
@@ -35,6 +37,21 @@ import workloads  # noqa: E402
 METRIC = "3D Euler ADER-DG DoF-updates/s on 1 GB300; mixed vs FP64 at same L2 err"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (nominal); a pure DFMA loop measured 1.20
 FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 128 FP32 lanes/SM, FMA = 2 flops
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+_PEAKS = _measured_peaks()
+# measured copy bandwidth (fallback 6.8 TB/s) and cuBLAS bf16 burst rate;
+# dense TF32 on the tensor cores is half the bf16 rate
+HBM_PEAK_GBS = float(_PEAKS.get("hbm_gbs", 6800.0))
+TF32_PEAK_TFLOPS = float(_PEAKS.get("bf16_tflops", 1900.0)) / 2
 
 # DRAM bytes (read + write) per cell of one predictor launch, from the ncu
 # captures summarised in profiles/ for the current kernel versions (small
@@ -81,6 +98,83 @@ def predictor_bytes_per_cell(dim, order, m):
     and the 2d face blocks (Q-bar and F-bar)."""
     n = order + 1
     return 8 * (2 * m * n ** dim + 2 * 2 * dim * m * n ** (dim - 1))
+
+
+def euler_speed_flops(dim):
+    """Flops of one Euler wave-speed estimate |v_d| + sqrt(gamma p / rho),
+    division and square root counted as one flop each: reciprocal of rho,
+    dim velocities, kinetic energy (2 dim), pressure (2), sound speed (3)."""
+    return 1 + dim + 2 * dim + 2 + 3 + 1
+
+
+def fp64_step_flops_per_cell(dim, order, m):
+    """Algorithmic FP64 flops per cell of one step outside the predictor:
+    Rusanov on the cell's dim faces (two wave speeds and 3 m flops per face
+    node), the corrector lifting (2 dim FMAs and one FMA per node and
+    variable) and the CFL rate (dim wave speeds per node)."""
+    n = order + 1
+    NS, NF = n ** dim, n ** (dim - 1)
+    riemann = dim * NF * (2 * euler_speed_flops(dim) + 3 * m)
+    corrector = NS * m * (4 * dim + 2)
+    rate = NS * (dim * euler_speed_flops(dim) + dim)
+    return riemann + corrector + rate
+
+
+def step_bytes_per_cell(dim, order, m):
+    """Minimum HBM bytes per cell of one step with the predictor fused with
+    the volume term: u read by the predictor, u* written and re-read, u
+    written by the corrector (4 m n^d doubles), and the face data: Q-bar and
+    F-bar written and read by the Riemann solves, F* written and read by the
+    corrector (11 m n^(d-1) doubles per face slot pair, d slot pairs)."""
+    n = order + 1
+    return 8 * (4 * m * n ** dim + 11 * dim * m * n ** (dim - 1))
+
+
+def contraction_tc_flops_per_cell(dim, order, iters, m):
+    """Tensor-core flops per cell of the tcgen05 predictor: per Picard slice
+    and direction the m n^(d-1) lines padded to M = 128 tiles, times N = 16
+    columns and K = 8 (the coordinate along the line, padded), 2 per MAC."""
+    n = order + 1
+    rows = m * n ** (dim - 1)
+    tiles = (rows + 127) // 128
+    slices = 1 + (iters - 1) * n
+    return slices * dim * tiles * 128 * 16 * 8 * 2
+
+
+# FP32 instructions per FP64 flop of the double-float predictor (the
+# compensated multiply-add of a contraction term: TwoProduct by FMA 2,
+# TwoSum 6, the low-part FMA and add 2, and the renormalisation amortised
+# over the sum, about 2).
+DF64_FP32_PER_FLOP = 6
+
+
+def step_roofline(prec, dim, order, m, ncells, step_s):
+    """Step-level bound: each term is the algorithmic work of one unit over
+    its measured or nominal peak; the binding term is the largest, and frac
+    = its time over the measured step time."""
+    iters = order + 1
+    pred = predictor_flops_per_cell(dim, order, iters, m) * ncells
+    terms = {"hbm": step_bytes_per_cell(dim, order, m) * ncells / (HBM_PEAK_GBS * 1e9),
+             "fp64_faces_corrector": fp64_step_flops_per_cell(dim, order, m) * ncells /
+             (FP64_PEAK_TFLOPS * 1e12)}
+    if prec == "fp64":
+        terms["fp64_faces_corrector"] += pred / (FP64_PEAK_TFLOPS * 1e12)
+        terms = {"hbm": terms["hbm"], "fp64_alu": terms["fp64_faces_corrector"]}
+    elif prec == "df64":
+        terms["fp32_predictor"] = DF64_FP32_PER_FLOP * pred / 2 / (FP32_PEAK_TFLOPS * 1e12)
+    elif prec == "fp32":
+        terms["fp32_predictor"] = pred / (FP32_PEAK_TFLOPS * 1e12)
+    else:
+        tc = contraction_tc_flops_per_cell(dim, order, iters, m) * ncells
+        products = 1 if prec == "tf32" else 3
+        terms["tensor_contractions"] = products * tc / (TF32_PEAK_TFLOPS * 1e12)
+        div = (1 + (iters - 1) * (order + 1)) * (order + 1) ** dim * dim * m * 2 * (order + 1)
+        terms["fp32_predictor_rest"] = (pred - div * ncells) / (FP32_PEAK_TFLOPS * 1e12)
+    bound = max(terms, key=terms.get)
+    return {"bound": bound, "bound_ms": terms[bound] * 1e3, "step_ms": step_s * 1e3,
+            "frac": terms[bound] / step_s, "terms_ms": {k: v * 1e3 for k, v in terms.items()},
+            "peaks": {"fp64_tflops": FP64_PEAK_TFLOPS, "fp32_tflops": FP32_PEAK_TFLOPS,
+                      "tf32_tflops": TF32_PEAK_TFLOPS, "hbm_gbs": HBM_PEAK_GBS}}
 
 
 def bind_near_gpu(torch, index):
@@ -225,8 +319,8 @@ def run_steps(s, wl, k, t_dev, step_base):
     dofs = 0
     for i in range(k):
         dofs += dofs_of(s)
+        t_dev.add_(s.dt)           # the step advances by the dt it reads
         s.step(1)
-        t_dev.add_(s.dt)
         j = step_base + i + 1
         if wl["remesh_every"] and j % wl["remesh_every"] == 0:
             t = float(t_dev.item())
@@ -238,12 +332,39 @@ def run_steps(s, wl, k, t_dev, step_base):
     return dofs
 
 
-def l2_error_vs_exact(s, u_dev, t):
+def run_steps_dd(sub, ex, wl, k, t_dev, step_base):
+    """run_steps for one rank's sub-domain of a partitioned mesh: the
+    exchange of partition-face data inside every step, dt as the minimum
+    over ranks, and remeshing with whole-mesh flags plus the migration of the
+    cells that change owner (DoF-updates of the owned cells)."""
+    from paper_1806_07984_gb300 import domain
+    s = sub.solver
+    dofs = 0
+    for i in range(k):
+        dofs += dofs_of(s)
+        t_dev.add_(s.dt)
+        domain.step_dist(sub, ex, 1)
+        j = step_base + i + 1
+        if wl["remesh_every"] and j % wl["remesh_every"] == 0:
+            t = float(t_dev.item())
+            r0 = time.perf_counter()
+            center = workloads.sphere_center(t)[:wl["dim"]]
+            flags = s.sphere_flags(center, wl["radius"])
+            domain.remesh_dist(sub, ex, flags)
+            s.classify(s.sphere_flags(center, wl["radius"]))
+            REMESH_LOG.append(time.perf_counter() - r0)
+    return dofs
+
+
+def l2_error_vs_exact(s, u_dev, t, init="bubble"):
     """Per-variable L2 error (GL quadrature) of the state against the exact
-    translated bubble at time t, relative to the L2 norm of the exact state."""
+    solution at time t (the translated bubble or vortex), relative to the L2
+    norm of the exact state."""
     import torch
     X = s.node_coords()
-    ex = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X, t=t), 0, 1))
+    q = workloads.density_bubble(X, t=t) if init == "bubble" else \
+        workloads.isentropic_vortex(X[0], X[1], t=t)
+    ex = np.ascontiguousarray(np.moveaxis(q, 0, 1))
     del X
     xi = s.nodes()
     w = np.polynomial.legendre.leggauss(s.n)[1] / 2.0
@@ -263,6 +384,62 @@ def l2_error_vs_exact(s, u_dev, t):
         norms.append(float(np.sqrt((nrm * vol).sum())))
     del xi
     return [e / nv for e, nv in zip(errs, norms)], got
+
+
+VAR_NAMES = {2: ["rho", "rho_u", "rho_v", "E"], 3: ["rho", "rho_u", "rho_v", "rho_w", "E"]}
+
+
+def precision_sweep(torch, wl, precs, steps, warmup, device, base=None):
+    """The same workload with each predictor precision: DoF-updates/s over
+    `steps` steps after `warmup` (remeshing included), the speed-up over the
+    FP64 step, the L2 error against the exact solution, per-variable relative
+    L2 and max error against the FP64 result, the predictor's launch time and
+    the step-level roofline.  `base` = (value, state, cells) of an FP64 run
+    of the same steps; without it the first entry of precs must be fp64."""
+    out = {}
+    names = VAR_NAMES[wl["dim"]]
+    stream = torch.cuda.current_stream()
+    for prec in precs:
+        if prec in ("tf32", "tf32x3", "bf16x3") and not (wl["dim"] == 3 and wl["order"] >= 5):
+            continue
+        sm_, u0m = build_problem(wl, prec, device)
+        sm_.set_state(torch.from_numpy(u0m).to(device))
+        sm_.compute_dt()
+        t_m = torch.zeros(1, dtype=torch.float64, device=device)
+        run_steps(sm_, wl, warmup, t_m, 0)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        dofs_m = run_steps(sm_, wl, steps, t_m, warmup)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        el_m = f0.elapsed_time(f1) / 1e3
+        err_m, state_m = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()), wl["init"])
+        value = dofs_m / el_m
+        entry = {"value": value, "unit": "DoF-updates/s", "ms_per_step": el_m / steps * 1e3,
+                 "l2_rel_err_vs_exact": dict(zip(names, err_m)), "status": sm_.status()}
+        if prec == "fp64" and base is None:
+            base = (value, state_m, sm_.cells())
+        else:
+            entry["speedup_vs_fp64"] = value / base[0]
+            if np.array_equal(sm_.cells(), base[2]):
+                entry["vs_fp64_per_var"] = {
+                    names[v]: {"rel_l2": float(np.linalg.norm(state_m[:, v] - base[1][:, v]) /
+                                               np.linalg.norm(base[1][:, v])),
+                               "rel_max": float(np.abs(state_m[:, v] - base[1][:, v]).max() /
+                                                np.abs(base[1][:, v]).max())}
+                    for v in range(sm_.nvar)}
+        t_pred = time_predictor(sm_, torch)
+        flops = predictor_flops_per_cell(sm_.dim, sm_.order, sm_.order + 1, sm_.nvar) * sm_.ncells
+        entry["predictor_launch_ms"] = t_pred * 1e3
+        entry["predictor_tflops"] = flops / t_pred / 1e12
+        entry["step_roofline"] = step_roofline(prec, sm_.dim, sm_.order, sm_.nvar, sm_.ncells,
+                                               el_m / steps)
+        out[prec] = entry
+        del state_m
+        sm_.close()
+    return out, base
 
 
 def batch_state(sides, orders, specs):
@@ -628,6 +805,40 @@ def reference_arm(args, wl_name, wl):
     print(json.dumps(line))
 
 
+def _g(x, digits=3):
+    return float(f"{x:.{digits}g}") if isinstance(x, (int, float)) else x
+
+
+def summarise(line):
+    """Compact digest of the line's sections (kept last in the JSON line):
+    per precision the speed-up over FP64, the density's L2 error against the
+    exact solution and against the FP64 result, and the step's roofline."""
+    out = {"fp64": _g(line["value"]), "remesh_ms": line["remesh"]["ms_each"],
+           "fp64_step_frac": None}
+
+    def digest(sec):
+        d = {}
+        for prec, e in sec.items():
+            if not isinstance(e, dict) or "value" not in e:
+                continue
+            ex = e.get("l2_rel_err_vs_exact", {})
+            r = e.get("step_roofline", {})
+            d[prec] = {"v": _g(e["value"]), "x": _g(e.get("speedup_vs_fp64", 1.0)),
+                       "err_rho": _g(ex.get("rho")) if ex else None,
+                       "vs64_rho": _g(e.get("vs_fp64_per_var", {}).get("rho", {}).get("rel_l2")),
+                       "bound": r.get("bound"), "frac": _g(r.get("frac"))}
+        return d
+    if line.get("mixed"):
+        out["n5"] = digest(line["mixed"])
+        out["fp64_step_frac"] = out["n5"].get("fp64", {}).get("frac")
+    cf = line.get("configs") or {}
+    if "euler3d-n7-amr" in cf:
+        out["n7"] = digest(cf["euler3d-n7-amr"])
+    if "euler2d-n3-vortex" in cf:
+        out["vortex_n3"] = digest({"fp64": cf["euler2d-n3-vortex"]})["fp64"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,6 +859,8 @@ def main():
                     help="run one side section alone and print its JSON object (no headline)")
     ap.add_argument("--ck-base", type=int, default=54, help="grid of the CK section (base^3)")
     ap.add_argument("--no-indicator", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 2D N=3 vortex and 3D N=7 sections")
     ap.add_argument("--pipeline", type=int, default=0,
                     help="enclave chunks per step (0 = library default, 1 = no pipelining)")
     ap.add_argument("--pipeline-ctas", type=int, default=0,
@@ -685,8 +898,20 @@ def main():
     u_dev = torch.from_numpy(u0).to(device)
     s.set_state(u_dev)
     s.compute_dt()
+    # N > 1: one sub-domain of the SFC partition per rank (the whole mesh and
+    # state were built on every rank; each keeps its owned cells)
+    sub = ex = None
+    if world > 1:
+        from paper_1806_07984_gb300 import domain
+        sub = domain.SubDomain(s, world, rank)
+        ex = domain.DistExchange()
+
+    def steps_fn(k, t, base):
+        if sub is not None:
+            return run_steps_dd(sub, ex, wl, k, t, base)
+        return run_steps(s, wl, k, t, base)
     t_dev = torch.zeros(1, dtype=torch.float64, device=device)
-    run_steps(s, wl, args.warmup, t_dev, 0)
+    steps_fn(args.warmup, t_dev, 0)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region -----------------------------------
@@ -701,7 +926,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     REMESH_LOG.clear()
-    dofs = run_steps(s, wl, args.steps, t_dev, args.warmup)
+    dofs = steps_fn(args.steps, t_dev, args.warmup)
     remesh_times = list(REMESH_LOG)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -742,14 +967,25 @@ def main():
     from paper_1806_07984_gb300 import ader as A
     e2e_steps = max(2, min(args.steps, 5))
     s2, u02 = build_problem(wl, args.precision, device)
-    host = torch.from_numpy(u02).pin_memory()
+    s2.set_state(u02)
+    s2.compute_dt()
+    sub2 = None
+    if world > 1:
+        from paper_1806_07984_gb300 import domain
+        sub2 = domain.SubDomain(s2, world, rank)
+        ex2 = domain.DistExchange()
+    host = s2.get_state().cpu().pin_memory()   # the owned cells (all of them at N = 1)
     del u02
-    s2.set_state(host)
-    s2.compute_dt()
+
+    def steps2(k, t, base):
+        if sub2 is not None:
+            return run_steps_dd(sub2, ex2, wl, k, t, base)
+        return run_steps(s2, wl, k, t, base)
     t_e2e = torch.zeros(1, dtype=torch.float64, device=device)
-    run_steps(s2, wl, 2, t_e2e, 0)          # untimed warm-up: an eager step, then the step graph
+    steps2(2, t_e2e, 0)                     # untimed warm-up: an eager step, then the step graph
     s2.set_state(host)
-    s2.compute_dt()
+    if sub2 is None:
+        s2.compute_dt()
     t_e2e.zero_()
     torch.cuda.synchronize()
     c0 = time.perf_counter()
@@ -759,7 +995,7 @@ def main():
         t_i = time.perf_counter()
         s2.set_state(host)
         h2d += host.numel() * 8
-        e2e_dofs += run_steps(s2, wl, 1, t_e2e, i)
+        e2e_dofs += steps2(1, t_e2e, i)
         if tuple(host.shape) != s2.state_shape():
             host = torch.empty(s2.state_shape(), dtype=torch.float64).pin_memory()
         A.ader_get_state(s2.ctx, host.data_ptr(), False, stream.cuda_stream)
@@ -767,64 +1003,32 @@ def main():
         e2e_each.append(round((time.perf_counter() - t_i) * 1e3, 1))
     torch.cuda.synchronize()
     e2e_time = time.perf_counter() - c0
+    e2e_total = float(e2e_dofs)
     if world > 1:
-        e2e_time, _ = reduce_over_ranks(torch, e2e_time, 0, device)
-    e2e = {"value": e2e_dofs * world / e2e_time, "unit": "DoF-updates/s",
+        e2e_time, e2e_total = reduce_over_ranks(torch, e2e_time, e2e_dofs, device)
+    e2e = {"value": e2e_total / e2e_time, "unit": "DoF-updates/s",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
            "steps": e2e_steps, "ms_each": e2e_each, "host_cpus": f"{len(near)} CPUs local to the GPU" if near else "unbound"}
     ncells, dofs_now, order, dim = s2.ncells, dofs_of(s2), s2.order, s2.dim
+    halo = sub.halo_bytes() if sub is not None else 0
+    ncells_all = A.ader_dd_info(s2.ctx)[2]
+    dofs_all = ncells_all * s2.nvar * s2.n ** s2.dim
     s2.close()
 
     # ---- mixed precision: FP32 / tensor-core predictors on the same workload ----
     mixed = None
-    if args.precision == "fp64" and args.mixed:
-        t_fp64 = float(t_dev.item())
-        err64, state64 = l2_error_vs_exact(s, s.get_state(), t_fp64)
+    if args.precision == "fp64" and args.mixed and world == 1:
+        err64, state64 = l2_error_vs_exact(s, s.get_state(), float(t_dev.item()), wl["init"])
         cells64 = s.cells()
         s.close()
         del u_dev
-        mixed = {}
-        names = ["rho", "rho_u", "rho_v", "rho_w", "E"]
-        for prec in args.mixed.split(","):
-            if prec in ("tf32", "tf32x3", "bf16x3") and not (wl["dim"] == 3 and wl["order"] >= 5):
-                continue
-            sm_, u0m = build_problem(wl, prec, device)
-            sm_.set_state(torch.from_numpy(u0m).to(device))
-            sm_.compute_dt()
-            t_m = torch.zeros(1, dtype=torch.float64, device=device)
-            run_steps(sm_, wl, args.warmup, t_m, 0)
-            torch.cuda.synchronize()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            dofs_m = run_steps(sm_, wl, args.steps, t_m, args.warmup)
-            f1.record(stream)
-            torch.cuda.synchronize()
-            el_m = f0.elapsed_time(f1) / 1e3
-            err_m, state_m = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()))
-            same_mesh = np.array_equal(sm_.cells(), cells64)
-            per_var = None
-            if same_mesh:
-                per_var = {}
-                for v in range(sm_.nvar):
-                    dv = state_m[:, v] - state64[:, v]
-                    per_var[names[v]] = {
-                        "rel_l2": float(np.linalg.norm(dv) / np.linalg.norm(state64[:, v])),
-                        "max_abs": float(np.abs(dv).max())}
-            t_pred_m = time_predictor(sm_, torch)
-            flops_m = predictor_flops_per_cell(sm_.dim, sm_.order, sm_.order + 1,
-                                               sm_.nvar) * sm_.ncells
-            mixed[prec] = {
-                "value": dofs_m / el_m, "unit": "DoF-updates/s", "ms_per_step": el_m / args.steps * 1e3,
-                "speedup_vs_fp64": (dofs_m / el_m) / value,
-                "l2_rel_err_vs_exact": err_m, "vs_fp64_per_var": per_var,
-                "status": sm_.status(), "predictor_launch_ms": t_pred_m * 1e3,
-                "predictor_tflops": flops_m / t_pred_m / 1e12,
-                "predictor_frac_of_fp32_peak": flops_m / t_pred_m / 1e12 / FP32_PEAK_TFLOPS}
-            del state_m
-            sm_.close()
-        mixed["fp64_l2_rel_err_vs_exact"] = err64
-        mixed["vars"] = names[:len(err64)]
+        names = VAR_NAMES[wl["dim"]]
+        mixed, _ = precision_sweep(torch, wl, args.mixed.split(","), args.steps, args.warmup,
+                                   device, base=(value, state64, cells64))
+        mixed["fp64"] = {"value": value, "l2_rel_err_vs_exact": dict(zip(names, err64)),
+                         "step_roofline": step_roofline("fp64", wl["dim"], wl["order"],
+                                                        len(names), ncells,
+                                                        elapsed / args.steps)}
         mixed["note"] = ("predictor arithmetic: df64 = double-float on the FP32 pipes, fp32 = FP32 "
                          "CUDA cores, tf32/tf32x3/bf16x3 = tcgen05 tensor cores; FP64 state, faces, "
                          "Riemann, corrector and CFL reduction in every mode")
@@ -832,6 +1036,21 @@ def main():
     else:
         s.close()
         del u_dev
+
+    # ---- the other workload shapes: config 1 (2D vortex, N=3) and config 3
+    # (3D AMR at N=7, FP64 against the mixed predictors) ----------------------
+    configs = None
+    if not args.no_configs and world == 1 and args.workload == "euler3d-n5-amr":
+        configs = {}
+        v1, _ = precision_sweep(torch, WORKLOADS["euler2d-n3-vortex"], ["fp64"], 20, 3, device)
+        configs["euler2d-n3-vortex"] = dict(v1["fp64"], workload=(
+            "2D Euler N=3, 27^2 periodic, isentropic vortex eps=5 on rho=1, v=(1,1), p=1, "
+            "20 steps after 3"))
+        precs3 = ["fp64"] + [p for p in args.mixed.split(",") if p]
+        v3, _ = precision_sweep(torch, WORKLOADS["euler3d-n7-amr"], precs3, 7, 3, device)
+        v3["workload"] = ("3D Euler N=7, base 27^3 + 2 levels around the bubble, 7 steps after 3 "
+                          "(a remesh inside)")
+        configs["euler3d-n7-amr"] = v3
 
     # ---- batched instances (one CUDA graph per run) --------------------------
     batched = None
@@ -849,16 +1068,17 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "dim": dim, "order": order,
-                       "cells": ncells, "dofs": dofs_now, "precision": args.precision,
-                       "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_now * 8 / 1e9),
+                       "cells": ncells_all, "dofs": dofs_all, "precision": args.precision,
+                       "parallelism": f"sfc{world}" if world > 1 else "single",
+                       "halo_bytes_per_step_rank0": halo,
+                       "l2": "inputs larger than L2 (state %.1f GB)" % (dofs_all * 8 / 1e9),
                        "remesh_every": wl["remesh_every"],
                        "pipeline_chunks": args.pipeline or 8,
-                       "pipeline_ctas_per_sm": args.pipeline_ctas or 2},
+                       "pipeline_ctas_per_sm": args.pipeline_ctas or 4},
             "remesh": {"count_in_timed_steps": len(remesh_times),
                        "ms_each": [round(x * 1e3, 2) for x in remesh_times],
                        "included_in_value": True,
@@ -866,11 +1086,12 @@ def main():
                                "reclassification; the paper's timings exclude remeshing"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
             "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter,
-            "ck": ck, "indicator": indicator}
+            "ck": ck, "indicator": indicator, "configs": configs}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, seconds=10.0,
                                                       cores=os.cpu_count() or 1)
+    line["summary"] = summarise(line)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

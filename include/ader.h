@@ -31,9 +31,12 @@
  *   - Numerical failures inside kernels (non-finite predictor output, rho <= 0
  *     or p <= 0, non-finite CFL rate) set bits of a device status word that
  *     ader_status_word() reads after synchronising.
- *   - ADER_ERR_OOM or ADER_ERR_CUDA from a call that may grow the context's
- *     cell buffers (ader_init, ader_remesh) can leave some of them released:
- *     the only call such a context accepts afterwards is ader_destroy.
+ *   - Growing the context's buffers allocates every new buffer before it
+ *     releases an old one.  ADER_ERR_OOM from ader_remesh (unpartitioned)
+ *     leaves the context as it was before the call: mesh, lists and state.
+ *     ADER_ERR_OOM or ADER_ERR_CUDA from ader_init, from ader_remesh on a
+ *     partitioned context, or ADER_ERR_CUDA from any call may leave the
+ *     context unusable: the only call it accepts afterwards is ader_destroy.
  *
  * Data layout (FP64 throughout at the boundary; c = cell, m = nvar,
  * n = order + 1 Gauss-Legendre nodes per direction, node index with x fastest,
@@ -123,7 +126,7 @@ typedef struct {
   double limiter_delta0;     /* relaxed maximum principle: delta = max(delta0, eps (max - min)); */
   double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
   int pipeline_chunks;       /* ader_step: enclave chunks K (0 selects 8, 1 disables); see ader_step */
-  int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 2) */
+  int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 4) */
   int eager_steps;           /* 1: ader_step launches every kernel itself instead of replaying a
                                 CUDA graph of one step (captured once per mesh and dt pointer) */
 } ader_config;
@@ -319,6 +322,13 @@ ader_status ader_sample(ader_ctx* ctx, int npts, const int32_t* cells, const dou
 ader_status ader_sample_adjoint(ader_ctx* ctx, int npts, const int32_t* cells,
                                 const double* weights, int var, const double* values,
                                 double* field, void* stream);
+
+/* Fault injection for tests (host side, no device fault): after `after`
+ * more successful device allocations, every allocation the library makes
+ * while growing buffers (ader_remesh, ader_classify, ader_partition) fails as
+ * if the device were out of memory; after < 0 switches it off.  Process-wide;
+ * the paper has no counterpart. */
+ader_status ader_debug_fail_allocations(int after);
 
 /* Number of kernel launches this context has enqueued so far. */
 ader_status ader_launch_count(ader_ctx* ctx, int64_t* out);

@@ -44,7 +44,7 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_mesh_pipeline", "ader_partition", "ader_dd_info", "ader_dd_cuts",
            "ader_halo_size", "ader_halo_pack", "ader_halo_unpack", "ader_migrate_size",
            "ader_migrate_pack", "ader_migrate_unpack", "ader_mesh_partition",
-           "ader_mesh_subdomain"]
+           "ader_mesh_subdomain", "ader_debug_fail_allocations"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -141,6 +141,7 @@ def lib():
         "ader_sample_adjoint": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
                                 ctypes.c_int),
         "ader_partition": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "ader_debug_fail_allocations": ([ctypes.c_int], ctypes.c_int),
         "ader_dd_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _i64p, _i64p,
                           _i64p, _i64p], ctypes.c_int),
         "ader_dd_cuts": ([_vp, _vp], ctypes.c_int),
@@ -580,3 +581,9 @@ def ader_mesh_partition(mesh, nranks, rank, dim):
         _ptr(out["children"]), _ptr(out["skeleton"]), _ptr(out["send_off"]), _ptr(out["send"]),
         _ptr(out["recv_off"]), _ptr(out["recv"])), "ader_mesh_subdomain")
     return out
+
+
+def ader_debug_fail_allocations(after):
+    """Fault injection for tests: the library's device allocations fail after
+    `after` more successes (after < 0: off)."""
+    _check(None, lib().ader_debug_fail_allocations(after), "ader_debug_fail_allocations")

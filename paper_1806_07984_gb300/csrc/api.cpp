@@ -136,71 +136,90 @@ cudaError_t do_transfer(ader_ctx* c, const TransferArgs& a, cudaStream_t s) {
   return c->cfg.dim == 2 ? transfer_acoustics2d(N, a, s) : transfer_acoustics3d(N, a, s);
 }
 
+// Fault injection for tests (ader_debug_fail_allocations): while >= 0, the
+// number of device allocations that still succeed; once it reaches 0 every
+// allocation of the library fails on the host with cudaErrorMemoryAllocation,
+// without reaching the driver.
+std::atomic<int> g_alloc_budget{-1};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  int b = g_alloc_budget.load();
+  while (b >= 0) {
+    if (b == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+// Capacity for `need` elements; the old buffer is released only once the new
+// one exists (contents are not kept: callers upload after growing).
 template <class T>
 cudaError_t grow(T** p, int64_t* cap, int64_t need) {
   if (need <= *cap && *p) return cudaSuccess;
   const int64_t nc = std::max<int64_t>(need + need / 4, 16);
+  void* q = nullptr;
+  const cudaError_t e = dev_alloc(&q, sizeof(T) * size_t(nc));
+  if (e != cudaSuccess) return e;
   if (*p) cudaFree(*p);
-  *p = nullptr;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * size_t(nc));
-  if (e == cudaSuccess) *cap = nc;
-  return e;
+  *p = static_cast<T*>(q);
+  *cap = nc;
+  return cudaSuccess;
 }
 
-// Cell-sized buffers for `need` cells; u (and ustar when keep_ustar) keep
-// their contents up to the old capacity.
+// Cell-sized buffers for `need` cells; u keeps its contents.  Every new
+// buffer is allocated before any old one is released, so a failure leaves
+// the context's buffers as they were.
 ader_status ensure_cells(ader_ctx* c, int64_t need) {
   if (need <= c->cap) return ADER_OK;
   const int64_t nc = need + need / 4;
   const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
   const size_t face_bytes = size_t(2 * c->cfg.dim) * c->M * c->NF * sizeof(double);
-  double* nu = nullptr;
-  CK(cudaMalloc(&nu, cell_bytes * size_t(nc)), "cudaMalloc u");
-  if (c->u) {
-    CK(cudaMemcpy(nu, c->u, cell_bytes * size_t(c->cap), cudaMemcpyDeviceToDevice), "copy u");
-    cudaFree(c->u);
-  }
-  c->u = nu;
-  cudaFree(c->ustar);
-  cudaFree(c->faceQ);
-  cudaFree(c->faceF);
-  cudaFree(c->fstar);
-  cudaFree(c->level);
-  cudaFree(c->all_cells);
-  cudaFree(c->skel_cells);
-  cudaFree(c->encl_cells);
-  cudaFree(c->corr_cells);
-  c->ustar = c->faceQ = c->faceF = c->fstar = nullptr;
-  c->level = nullptr;
-  c->all_cells = c->skel_cells = c->encl_cells = c->corr_cells = nullptr;
-  CK(cudaMalloc(&c->ustar, cell_bytes * size_t(nc)), "cudaMalloc ustar");
-  CK(cudaMalloc(&c->faceQ, face_bytes * size_t(nc)), "cudaMalloc faceQ");
-  CK(cudaMalloc(&c->faceF, face_bytes * size_t(nc)), "cudaMalloc faceF");
-  CK(cudaMalloc(&c->fstar, face_bytes * size_t(nc)), "cudaMalloc fstar");
-  CK(cudaMalloc(&c->level, size_t(nc)), "cudaMalloc level");
-  CK(cudaMalloc(&c->all_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
-  CK(cudaMalloc(&c->skel_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
-  CK(cudaMalloc(&c->encl_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
-  CK(cudaMalloc(&c->corr_cells, sizeof(int32_t) * size_t(nc)), "cudaMalloc lists");
+  const size_t N = size_t(nc);
+  std::vector<std::pair<void**, size_t>> req = {
+      {(void**)&c->u, cell_bytes * N},        {(void**)&c->ustar, cell_bytes * N},
+      {(void**)&c->faceQ, face_bytes * N},    {(void**)&c->faceF, face_bytes * N},
+      {(void**)&c->fstar, face_bytes * N},    {(void**)&c->level, N},
+      {(void**)&c->all_cells, 4 * N},         {(void**)&c->skel_cells, 4 * N},
+      {(void**)&c->encl_cells, 4 * N},        {(void**)&c->corr_cells, 4 * N}};
   if (c->cfg.limiter) {
-    for (void* p : {(void*)c->u_old, (void*)c->bounds, (void*)c->lim_flags, (void*)c->lim_list,
-                    (void*)c->fix_list, (void*)c->nbr, (void*)c->force})
-      if (p) cudaFree(p);
-    c->u_old = c->bounds = nullptr;
-    c->lim_flags = nullptr;
-    c->lim_list = c->fix_list = c->nbr = nullptr;
-    c->force = nullptr;
-    CK(cudaMalloc(&c->u_old, cell_bytes * size_t(nc)), "cudaMalloc limiter backup");
-    CK(cudaMalloc(&c->bounds, sizeof(double) * 2 * c->M * size_t(nc)), "cudaMalloc limiter bounds");
-    CK(cudaMalloc(&c->lim_flags, sizeof(uint32_t) * size_t(nc)), "cudaMalloc limiter flags");
-    CK(cudaMalloc(&c->lim_list, sizeof(int32_t) * size_t(nc)), "cudaMalloc limiter lists");
-    CK(cudaMalloc(&c->fix_list, sizeof(int32_t) * size_t(nc)), "cudaMalloc limiter lists");
-    CK(cudaMalloc(&c->nbr, sizeof(int32_t) * 2 * c->cfg.dim * size_t(nc)), "cudaMalloc neighbours");
-    CK(cudaMalloc(&c->force, size_t(nc)), "cudaMalloc limiter force");
-    CK(cudaMemset(c->lim_flags, 0, sizeof(uint32_t) * size_t(nc)), "clear limiter flags");
-    CK(cudaMemset(c->force, 0, size_t(nc)), "clear limiter force");
-    c->force_set = false;
+    req.insert(req.end(), {{(void**)&c->u_old, cell_bytes * N},
+                           {(void**)&c->bounds, sizeof(double) * 2 * c->M * N},
+                           {(void**)&c->lim_flags, sizeof(uint32_t) * N},
+                           {(void**)&c->lim_list, 4 * N},
+                           {(void**)&c->fix_list, 4 * N},
+                           {(void**)&c->nbr, 4 * size_t(2 * c->cfg.dim) * N},
+                           {(void**)&c->force, N}});
   }
+  std::vector<void*> fresh(req.size(), nullptr);
+  auto release = [&]() {
+    for (void* p : fresh)
+      if (p) cudaFree(p);
+  };
+  for (size_t i = 0; i < req.size(); ++i) {
+    const cudaError_t e = dev_alloc(&fresh[i], req[i].second);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(c, e, "cudaMalloc cell buffers");
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (c->u) e = cudaMemcpy(fresh[0], c->u, cell_bytes * size_t(c->cap), cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && c->cfg.limiter) {
+    e = cudaMemset(fresh[12], 0, sizeof(uint32_t) * N);
+    if (e == cudaSuccess) e = cudaMemset(fresh[16], 0, N);
+  }
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "copy cell buffers");
+  }
+  for (size_t i = 0; i < req.size(); ++i) {
+    if (*req[i].first) cudaFree(*req[i].first);
+    *req[i].first = fresh[i];
+  }
+  if (c->cfg.limiter) c->force_set = false;
   c->cap = nc;
   return ADER_OK;
 }
@@ -241,9 +260,10 @@ ader_status upload_mesh(ader_ctx* c) {
   int64_t pc_old = c->par_cap;
   CK(grow(&c->parents, &c->par_cap, int64_t(t.parents.size())), "cudaMalloc parents");
   if (c->par_cap != pc_old || !c->child_fine) {
-    cudaFree(c->child_fine);
-    c->child_fine = nullptr;
-    CK(cudaMalloc(&c->child_fine, sizeof(int32_t) * size_t(c->par_cap * S)), "cudaMalloc children");
+    void* q = nullptr;
+    CK(dev_alloc(&q, sizeof(int32_t) * size_t(c->par_cap * S)), "cudaMalloc children");
+    if (c->child_fine) cudaFree(c->child_fine);
+    c->child_fine = static_cast<int32_t*>(q);
   }
   if (!t.parents.empty()) {
     CK(cudaMemcpy(c->parents, t.parents.data(), sizeof(ParentFace) * t.parents.size(),
@@ -736,7 +756,7 @@ ader_status step_pipelined(ader_ctx* c, double* dt_dev) {
   CK(do_predict(c, ps, c->s_hi), "skeleton predictor");
   ader_status st = enqueue_riemann(c, ADER_SKELETON, c->s_hi);
   if (st != ADER_OK) return st;
-  const int cap = c->num_sms * (c->cfg.pipeline_ctas > 0 ? c->cfg.pipeline_ctas : 2);
+  const int cap = c->num_sms * (c->cfg.pipeline_ctas > 0 ? c->cfg.pipeline_ctas : 4);
   auto correct_group = [&](int g) -> ader_status {
     const int64_t b = t.corr_off[size_t(g)], e = t.corr_off[size_t(g) + 1];
     if (e > b) {
@@ -984,27 +1004,46 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   const int64_t C_old = int64_t(c->tree.cells.size());
   std::vector<TransferItem> plan;
   std::vector<int32_t> kids;
+  // The mesh before the call: restored, with its device lists, when the
+  // device side cannot follow (every buffer is allocated before an old one is
+  // released, so u still holds the old state then).
+  Tree saved = c->tree;
   if (!c->tree.remesh(flags, &plan, &kids)) {
     c->err = c->tree.error();
+    c->tree = std::move(saved);
     return ADER_ERR_MESH;
   }
   const int64_t C_new = int64_t(c->tree.cells.size());
   c->force_set = false;
+  double* old_u = nullptr;
+  bool own_old = false;
+  auto undo = [&](ader_status st) {
+    const std::string why = c->err;
+    if (own_old) cudaFree(old_u);
+    c->tree = std::move(saved);
+    upload_mesh(c);  // the old mesh's lists fit the capacities already there
+    c->err = why;
+    return st;
+  };
   // Keep the old state while the mesh lists are uploaded: in u* (free between
   // steps) when the cell buffers keep their capacity, else in a new buffer.
   const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
   const bool in_place = C_new <= c->cap;
-  double* old_u = in_place ? c->ustar : nullptr;
-  if (!in_place)
-    CK(cudaMalloc(&old_u, cell_bytes * size_t(std::max<int64_t>(C_old, 1))), "cudaMalloc remesh");
-  CK(cudaMemcpy(old_u, c->u, cell_bytes * size_t(C_old), cudaMemcpyDeviceToDevice), "copy u");
-  ader_status st = upload_mesh(c);
-  if (st != ADER_OK) {
-    if (!in_place) cudaFree(old_u);
-    return st;
+  old_u = in_place ? c->ustar : nullptr;
+  if (!in_place) {
+    void* q = nullptr;
+    const cudaError_t ea = dev_alloc(&q, cell_bytes * size_t(std::max<int64_t>(C_old, 1)));
+    if (ea != cudaSuccess) return undo(cuda_fail(c, ea, "cudaMalloc remesh"));
+    old_u = static_cast<double*>(q);
+    own_old = true;
   }
-  CK(grow(&c->plan_dev, &c->plan_cap, int64_t(plan.size())), "cudaMalloc plan");
-  CK(grow(&c->kids_dev, &c->kids_cap, std::max<int64_t>(int64_t(kids.size()), 1)), "cudaMalloc kids");
+  cudaError_t ec = cudaMemcpy(old_u, c->u, cell_bytes * size_t(C_old), cudaMemcpyDeviceToDevice);
+  if (ec != cudaSuccess) return undo(cuda_fail(c, ec, "copy u"));
+  ader_status st = upload_mesh(c);
+  if (st != ADER_OK) return undo(st);
+  ec = grow(&c->plan_dev, &c->plan_cap, int64_t(plan.size()));
+  if (ec == cudaSuccess) ec = grow(&c->kids_dev, &c->kids_cap, std::max<int64_t>(int64_t(kids.size()), 1));
+  if (ec != cudaSuccess) return undo(cuda_fail(c, ec, "cudaMalloc plan"));
   TransferItem* d_plan = c->plan_dev;
   int32_t* d_kids = c->kids_dev;
   CK(cudaMemcpy(d_plan, plan.data(), sizeof(TransferItem) * plan.size(), cudaMemcpyHostToDevice),
@@ -1023,7 +1062,7 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   a.B = c->B;
   cudaError_t e = do_transfer(c, a, nullptr);
   cudaError_t e2 = cudaDeviceSynchronize();
-  if (!in_place) cudaFree(old_u);
+  if (own_old) cudaFree(old_u);
   if (e != cudaSuccess) return cuda_fail(c, e, "transfer");
   if (e2 != cudaSuccess) return cuda_fail(c, e2, "transfer sync");
   return ADER_OK;
@@ -1194,6 +1233,11 @@ ader_status ader_limiter_refine_flags(ader_ctx* c, int8_t* flags) {
   std::vector<uint8_t> troubled(C);
   for (size_t i = 0; i < C; ++i) troubled[i] = (lf[i] & (kLimited | kKeptAtTransition)) ? 1 : 0;
   c->tree.refine_around(troubled.data(), flags);
+  return ADER_OK;
+}
+
+ader_status ader_debug_fail_allocations(int after) {
+  g_alloc_budget.store(after < 0 ? -1 : after);
   return ADER_OK;
 }
 

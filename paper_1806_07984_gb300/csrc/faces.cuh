@@ -17,8 +17,8 @@
 // * transfer      - remesh volume transfer: copy, interpolate into a child,
 //                   or L2-project 3^d children onto the parent.
 // All in FP64.  Conforming faces: 32/G faces per warp for faces of at most 32
-// nodes (G lanes each), 8 faces per CTA for 36 or 49 nodes; child faces: one
-// warp per face (lanes over face nodes).
+// nodes (G lanes each), 128 / NF faces per 128-thread CTA for 36 or 49 nodes;
+// child faces: one warp per face (lanes over face nodes).
 #pragma once
 #include "kernels.h"
 #include "pde.cuh"
@@ -126,13 +126,16 @@ __global__ void riemann_conf_kernel(const RiemannArgs a) {
 }
 
 // Faces whose node count is above 32 and not a multiple of 32 (3D, N = 5, 6):
-// 8 faces per CTA, one thread per face node, the speed of each face reduced
-// with shared-memory atomics on the FP64 bit pattern (non-negative values);
-// no lane idles across the two passes a warp per face would take.
+// one thread per face node, the speed of each face reduced with shared-memory
+// atomics on the FP64 bit pattern (non-negative values); no lane idles
+// across the two passes a warp per face would take.  Faces per CTA: as many as
+// fit in 128 threads, so that a CTA (about 7k registers) fits on an SM beside
+// two CTAs of the FP32 predictor (57k) and the face solves of the enclave
+// pipeline overlap the predictor instead of displacing it.
 template <int NF>
 struct FaceBlock {
   static constexpr bool kUse = NF > 32 && NF % 32 != 0;
-  static constexpr int FPC = 8;
+  static constexpr int FPC = NF >= 128 ? 1 : 128 / NF;
   static constexpr int THREADS = (FPC * NF + 31) / 32 * 32;
 };
 
@@ -388,18 +391,21 @@ __device__ __forceinline__ void lift_node(const double* ustar, const double* fst
   }
 }
 
+// Corrector CTAs: 128 threads over the flat (cell, node) index, grid-stride.
+// A CTA (about 7k registers) fits beside two CTAs of the FP32 predictor, so
+// the correctors of the enclave pipeline run on the FP64 pipe next to them.
+constexpr int kCorrectThreads = 128;
+
 template <int DIM, int N, class PDE, bool UPDATE>
-__global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS) correct_kernel(const CorrectArgs a) {
+__global__ void __launch_bounds__(kCorrectThreads) correct_kernel(const CorrectArgs a) {
   using SH = PredictShape<DIM, N>;
-  constexpr int NS = SH::NS, CPB = SH::CPB, M = PDE::M;
-  const int tid = threadIdx.x;
-  const int cl = tid / NS;
-  const int node = tid - cl * NS;
-  const int64_t nblk = (a.ncells + CPB - 1) / CPB;
+  constexpr int NS = SH::NS, M = PDE::M;
+  const int64_t total = a.ncells * NS;
   double rate = 0.0;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int64_t idx = blk * CPB + cl;
-    if (idx >= a.ncells || node >= NS) continue;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t idx = i / NS;
+    const int node = int(i - idx * NS);
     const int64_t cell = a.cells ? int64_t(a.cells[idx]) : idx;
     const int lv = int(a.level[cell]);
     double q[M];
@@ -600,9 +606,9 @@ template <int DIM, int N, class PDE, bool UPDATE>
 cudaError_t launch_correct_t(const CorrectArgs& a, cudaStream_t s) {
   using SH = PredictShape<DIM, N>;
   if (a.ncells == 0) return cudaSuccess;
-  int64_t blocks = (a.ncells + SH::CPB - 1) / SH::CPB;
+  int64_t blocks = (a.ncells * SH::NS + kCorrectThreads - 1) / kCorrectThreads;
   if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
-  correct_kernel<DIM, N, PDE, UPDATE><<<unsigned(blocks), SH::THREADS, 0, s>>>(a);
+  correct_kernel<DIM, N, PDE, UPDATE><<<unsigned(blocks), kCorrectThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
