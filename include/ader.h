@@ -303,12 +303,13 @@ ader_status ader_limiter_refine_flags(ader_ctx* ctx, int8_t* flags);
  * linear map u(T) -> u(T+dt) of ader_step/ader_predict+ader_riemann+
  * ader_correct for linear acoustics (ADER_ACOUSTICS) with the dt stored at
  * dt_dev.  Each task of Eq. (4) is transposed in reverse order (corrector
- * lifting, Rusanov with s = c = 1, predictor volume term and face
- * extrapolation, time averages, and the Picard iterations unrolled with the
- * forward count, or the Cauchy-Kowalevski sum transposed by Horner's
- * scheme).  FP64 only.  Needs a mesh without resolution transitions; lambda
- * arrays are device [c][var][node] and must not alias.  Uses the context's
- * face buffers as scratch. */
+ * lifting, Rusanov with s = c = 1, at resolution transitions (Sec. 2.3) the
+ * restriction, child-face Rusanov and prolongation, then the predictor volume
+ * term and face extrapolation, time averages, and the Picard iterations
+ * unrolled with the forward count, or the Cauchy-Kowalevski sum transposed
+ * by Horner's scheme).  FP64 only; any adaptive mesh, not a partitioned
+ * context.  lambda arrays are device [c][var][node] and must not alias.  Uses
+ * the context's face buffers as scratch. */
 ader_status ader_adjoint_step(ader_ctx* ctx, const double* lambda_in, double* lambda_out,
                               const double* dt_dev, void* stream);
 

@@ -1,5 +1,5 @@
-// Discrete adjoint of one ADER-DG step for linear acoustics on meshes
-// without resolution transitions.
+// Discrete adjoint of one ADER-DG step for linear acoustics on adaptive
+// meshes.
 //
 // For a linear PDE the step u -> u(T+dt) of Eq. (4) is a linear map A
 // (Picard with a fixed iteration count, Rusanov with the exact speed s = c = 1,
@@ -8,6 +8,10 @@
 //   corrector   u+ = u* + Lift(F*)          ->  u*_bar = lambda, F*_bar = Lift^T lambda
 //   Riemann     F* = (F_L + F_R)/2 - s (Q_R - Q_L)/2 on every conforming face
 //                                          ->  (Q-bar, F-bar)_bar on both face slots
+//   transition  virtual face = P_s (coarse face), Rusanov on each child face,
+//               coarse F* = sum_s R_s F*_s (Sec. 2.3)
+//                                          ->  R_s^T into each child's F*_bar,
+//               Rusanov transposed, P_s^T summed into the coarse slot
 //   predictor   u* = u + dt V F-bar, faces = E (Q-bar, F-bar), Q-bar/F-bar from
 //               the Picard iterate          ->  lambda_out = u*_bar + (Picard,
 //               time average, extrapolation and volume term transposed)
@@ -79,6 +83,64 @@ __global__ void adjoint_riemann_kernel(const AdjointArgs a) {
     a.faceQ_bar[oL + v * NF] = 0.5 * s * Fb;
     a.faceF_bar[oR + v * NF] = 0.5 * Fb;
     a.faceQ_bar[oR + v * NF] = -0.5 * s * Fb;
+  }
+}
+
+// Transitions transposed, one CTA per parent face: the restriction (the
+// coarse slot's F*_bar reaches each child face through R_s^T), Rusanov with
+// s = 1 on the child faces, and the prolongation of the coarse face data
+// (P_s^T summed over the children).  The fine cells' slots facing the coarse
+// cell and the coarse cell's slot belong to this family alone, so each is
+// written once, as the conforming faces' slots are.
+template <int DIM, int N, int M>
+__global__ void adjoint_transition_kernel(const AdjointArgs a) {
+  constexpr int n = N + 1, NF = ipow(n, DIM - 1), S = DIM == 3 ? 9 : 3, nb = DIM == 3 ? n : 1;
+  __shared__ double gbar[S][M][NF];  // total adjoint of F* on each child face
+  const int64_t p = blockIdx.x;
+  if (p >= a.nparents) return;
+  const ParentFace pf = a.parents[p];
+  const int d = pf.dir, cs = pf.coarse_side;
+  const int64_t oC = (int64_t(pf.coarse) * 2 * DIM + 2 * d + cs) * M * NF;
+  const double* GC = a.fstar_bar + oC;
+  const double s = 1.0;  // Rusanov speed of acoustics with c = 1
+  // Q-bar_bar factors: the fine side is right of the face when the coarse
+  // cell is on the left (cs = 1), left of it otherwise
+  const double qf = cs == 1 ? -0.5 * s : 0.5 * s;
+  for (int t = threadIdx.x; t < S * NF; t += blockDim.x) {
+    const int sigma = t / NF, fn = t - sigma * NF;
+    const int s0 = sigma % 3, s1 = sigma / 3;
+    const int i = fn % n, j = fn / n;
+    const int64_t fine = a.child_fine[p * S + sigma];
+    const int64_t oF = (fine * 2 * DIM + 2 * d + (1 - cs)) * M * NF;
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      double g = a.fstar_bar[oF + v * NF + fn];
+      for (int ib = 0; ib < nb; ++ib) {
+        const double r1 = DIM == 3 ? a.B.R[s1][ib][j] : 1.0;
+        for (int ia = 0; ia < n; ++ia) g = fma(a.B.R[s0][ia][i] * r1, GC[v * NF + ia + n * ib], g);
+      }
+      gbar[sigma][v][fn] = g;
+      a.faceF_bar[oF + v * NF + fn] = 0.5 * g;
+      a.faceQ_bar[oF + v * NF + fn] = qf * g;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NF; t += blockDim.x) {
+    const int i = t % n, j = t / n;
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      double f = 0.0;
+      for (int sigma = 0; sigma < S; ++sigma) {
+        const int s0 = sigma % 3, s1 = sigma / 3;
+        for (int ib = 0; ib < nb; ++ib) {
+          const double p1 = DIM == 3 ? a.B.P[s1][ib][j] : 1.0;
+          for (int ia = 0; ia < n; ++ia)
+            f = fma(a.B.P[s0][ia][i] * p1, gbar[sigma][v][ia + n * ib], f);
+        }
+      }
+      a.faceF_bar[oC + v * NF + t] = 0.5 * f;
+      a.faceQ_bar[oC + v * NF + t] = -qf * f;
+    }
   }
 }
 
@@ -283,6 +345,9 @@ cudaError_t launch_adjoint_t(const AdjointArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int64_t t2 = a.nconf * NF;
   if (t2 > 0) adjoint_riemann_kernel<DIM, N, M><<<unsigned((t2 + 255) / 256), 256, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.nparents > 0) adjoint_transition_kernel<DIM, N, M><<<unsigned(a.nparents), 128, 0, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adjoint_predict_kernel<DIM, N, M>

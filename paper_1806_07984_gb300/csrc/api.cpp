@@ -1147,8 +1147,8 @@ ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out
     c->err = "the adjoint step is implemented for linear acoustics in FP64";
     return ADER_ERR_ARG;
   }
-  if (!c->tree.parents.empty() || c->partitioned) {
-    c->err = "the adjoint step needs an unpartitioned mesh without resolution transitions";
+  if (c->partitioned) {
+    c->err = "the adjoint step needs an unpartitioned mesh";
     return ADER_ERR_ARG;
   }
   AdjointArgs a{};
@@ -1159,6 +1159,9 @@ ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out
   a.faceF_bar = c->faceF;
   a.conf = c->conf;
   a.nconf = int64_t(c->tree.conf.size());
+  a.parents = c->parents;
+  a.child_fine = c->child_fine;
+  a.nparents = int64_t(c->tree.parents.size());
   a.level = c->level;
   a.ncells = int64_t(c->tree.cells.size());
   a.dt = dt_dev;
@@ -1166,7 +1169,7 @@ ader_status ader_adjoint_step(ader_ctx* c, const double* lam_in, double* lam_out
   a.scheme = c->cfg.predictor;
   std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
   a.B = c->B;
-  c->launches += 3;
+  c->launches += c->tree.parents.empty() ? 3 : 4;
   CK(launch_adjoint(c->cfg.dim, c->cfg.order, a, static_cast<cudaStream_t>(stream)), "adjoint step");
   return ADER_OK;
 }

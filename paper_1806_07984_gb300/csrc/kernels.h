@@ -191,6 +191,9 @@ struct AdjointArgs {
   double* faceF_bar;
   const ConfFace* conf;
   int64_t nconf;
+  const ParentFace* parents;  // resolution transitions
+  const int32_t* child_fine;  // [parent * 3^(d-1) + sigma]
+  int64_t nparents;
   const int8_t* level;
   int64_t ncells;
   const double* dt;

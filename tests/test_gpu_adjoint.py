@@ -11,25 +11,45 @@ from gpu_helpers import lib_keys, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def solver_for(dim, order, base, iters, predictor="picard"):
+def solver_for(dim, order, base, iters, predictor="picard", max_level=0):
     from paper_1806_07984_gb300 import Solver
-    return Solver(dim, order, "acoustics", base=(base,) * 3, max_level=0,
+    return Solver(dim, order, "acoustics", base=(base,) * 3, max_level=max_level,
                   cfl=workloads.ADER_CFL[order], picard_iters=iters, predictor=predictor)
 
 
-@pytest.mark.parametrize("dim,order,base,predictor", [(3, 2, 2, "picard"), (2, 3, 3, "picard"),
-                                                      (3, 2, 2, "ck"), (2, 4, 3, "ck")])
-def test_adjoint_equals_transpose_of_oracle_step(dim, order, base, predictor):
+def amr_pair(dim, order, base, iters, predictor, center, radius, levels=1):
+    """Library context and oracle mesh refined the same way around a ball."""
+    s = solver_for(dim, order, base, iters, predictor, max_level=levels)
+    m = omesh.Mesh(dim, (base,) * dim, levels)
+    for _ in range(levels):
+        fl = omesh.sphere_flags(m, center, radius)
+        s.remesh(fl[np.array([m.index[k] for k in lib_keys(s)])])
+        m.remesh(np.zeros((len(m.cells), 1) + (2,) * dim), fl, obasis.Basis(1))
+    assert sorted(lib_keys(s)) == m.cells
+    return s, m
+
+
+# uniform meshes, and meshes with one refined region (resolution transitions:
+# the adjoint of the prolongation, child-face Rusanov and restriction)
+@pytest.mark.parametrize("dim,order,base,predictor,amr", [
+    (3, 2, 2, "picard", False), (2, 3, 3, "picard", False), (3, 2, 2, "ck", False),
+    (2, 4, 3, "ck", False), (2, 2, 3, "picard", True), (2, 3, 3, "ck", True),
+    (3, 1, 3, "picard", True)])
+def test_adjoint_equals_transpose_of_oracle_step(dim, order, base, predictor, amr):
     import torch
     from paper_1806_07984_gb300 import ader as A
     iters = dim * order + 1
-    s = solver_for(dim, order, base, iters, predictor)
-    m = omesh.Mesh(dim, (base,) * dim, 0)
+    if amr:
+        s, m = amr_pair(dim, order, base, iters, predictor, (0.5, 0.5, 0.5)[:dim], 0.1)
+        assert s.mesh_info()[3] > 0
+    else:
+        s = solver_for(dim, order, base, iters, predictor)
+        m = omesh.Mesh(dim, (base,) * dim, 0)
     perm = np.array([m.index[k] for k in lib_keys(s)])
     B = obasis.Basis(order)
     P = opde.Acoustics(dim)
     shape = (len(m.cells), dim + 1) + (B.n,) * dim
-    dt = workloads.ADER_CFL[order] / (dim * base)
+    dt = workloads.ADER_CFL[order] / (dim * base * (3 if amr else 1))
     size = int(np.prod(shape))
     Amat = np.zeros((size, size))
     for j in range(size):
@@ -142,4 +162,30 @@ def test_ck_gradient_vs_central_differences():
         fd = (lp - lm) / 2e-6
         an = float((u.grad * v).sum())
         assert abs(fd - an) <= 1e-5 * abs(an), (k, fd, an)
+    s.close()
+
+
+@pytest.mark.parametrize("predictor", ["picard", "ck"])
+def test_dot_product_identity_amr_mesh(predictor):
+    """<A x, y> = <x, A^T y> on a 3D N=4 acoustics mesh with two levels of
+    refinement around a ball (hanging faces on both levels)."""
+    import torch
+    from paper_1806_07984_gb300 import ader as A
+    order = 4
+    s, m = amr_pair(3, order, 9, 3 * order + 1, predictor, (0.45, 0.5, 0.55), 0.15, levels=2)
+    assert s.mesh_info()[3] > 0
+    shape = s.state_shape()
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(shape, dtype=torch.float64, device="cuda", generator=g)
+    y = torch.randn(shape, dtype=torch.float64, device="cuda", generator=g)
+    s.set_state(x)
+    s.compute_dt()
+    dt = s.dt.clone()
+    s.predict(); s.riemann(); s.correct(torch.zeros_like(dt))
+    Ax = s.get_state()
+    Aty = torch.empty_like(y)
+    A.ader_adjoint_step(s.ctx, y, Aty, dt)
+    lhs = float((Ax * y).sum())
+    rhs = float((x * Aty).sum())
+    assert abs(lhs - rhs) <= 1e-12 * float(Ax.norm() * y.norm())
     s.close()
