@@ -299,6 +299,21 @@ ader_status ader_limiter_force(ader_ctx* ctx, const uint8_t* force);
  * ADER_ERR_ARG when the context has no limiter. */
 ader_status ader_limiter_refine_flags(ader_ctx* ctx, int8_t* flags);
 
+/* One limited step that leaves no troubled cell at a resolution transition
+ * (the paper keeps adaptivity out of FV regions by refining the DG solution
+ * down to the FV level near shocks, Sec. 6).  The step runs (ader_step with
+ * the limiter); when a troubled cell has a non-conforming face (kept its DG
+ * candidate, limiter flag bit 2), the state goes back to u(T), the mesh is
+ * refined around the troubled cells (they and their face neighbours below
+ * max_level; nothing coarsens), dt is recomputed from u(T) on the refined
+ * mesh into *dt_dev, and the step runs again, at most max_rounds times.
+ * *rounds (may be NULL) receives the refinements made; after the last step
+ * *dt_dev holds its dt_next and the status word its bits (those of discarded
+ * attempts are dropped).  Needs cfg.limiter; not on a partitioned context.
+ * Synchronises the device. */
+ader_status ader_step_refining(ader_ctx* ctx, double* dt_dev, int max_rounds, int* rounds,
+                               void* stream);
+
 /* Discrete adjoint of one step: *lambda_out = A^T lambda_in, where A is the
  * linear map u(T) -> u(T+dt) of ader_step/ader_predict+ader_riemann+
  * ader_correct for linear acoustics (ADER_ACOUSTICS) with the dt stored at

@@ -44,7 +44,7 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_mesh_pipeline", "ader_partition", "ader_dd_info", "ader_dd_cuts",
            "ader_halo_size", "ader_halo_pack", "ader_halo_unpack", "ader_migrate_size",
            "ader_migrate_pack", "ader_migrate_unpack", "ader_mesh_partition",
-           "ader_mesh_subdomain", "ader_debug_fail_allocations"]
+           "ader_mesh_subdomain", "ader_debug_fail_allocations", "ader_step_refining"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -142,6 +142,7 @@ def lib():
                                 ctypes.c_int),
         "ader_partition": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "ader_debug_fail_allocations": ([ctypes.c_int], ctypes.c_int),
+        "ader_step_refining": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp], ctypes.c_int),
         "ader_dd_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _i64p, _i64p,
                           _i64p, _i64p], ctypes.c_int),
         "ader_dd_cuts": ([_vp, _vp], ctypes.c_int),
@@ -587,3 +588,12 @@ def ader_debug_fail_allocations(after):
     """Fault injection for tests: the library's device allocations fail after
     `after` more successes (after < 0: off)."""
     _check(None, lib().ader_debug_fail_allocations(after), "ader_debug_fail_allocations")
+
+
+def ader_step_refining(ctx, dt, max_rounds, stream=None):
+    """One limited step with immediate refinement around troubled cells at
+    resolution transitions; returns the number of refinements."""
+    r = ctypes.c_int()
+    _check(ctx, lib().ader_step_refining(ctx, _ptr(dt), max_rounds, ctypes.byref(r), stream),
+           "ader_step_refining")
+    return r.value

@@ -1227,6 +1227,45 @@ ader_status ader_limiter_force(ader_ctx* c, const uint8_t* force) {
   return ADER_OK;
 }
 
+ader_status ader_step_refining(ader_ctx* c, double* dt_dev, int max_rounds, int* rounds, void* stream) {
+  if (!c || !dt_dev || max_rounds < 0 || !c->cfg.limiter || c->partitioned) return ADER_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaDeviceSynchronize(), "sync before refining step");
+  // status bits of a discarded attempt are dropped: the word is reset to its
+  // value before the call ahead of every repeat
+  uint32_t status0 = 0;
+  CK(cudaMemcpy(&status0, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read status");
+  int r = 0;
+  for (;;) {
+    ader_status st = ader_step(c, 1, dt_dev, stream);
+    if (st != ADER_OK) return st;
+    CK(cudaStreamSynchronize(s), "refining step sync");
+    CK(cudaDeviceSynchronize(), "refining step sync");
+    const size_t C = c->tree.cells.size();
+    std::vector<uint32_t> lf(C);
+    if (C) CK(cudaMemcpy(lf.data(), c->lim_flags, sizeof(uint32_t) * C, cudaMemcpyDeviceToHost), "limiter flags");
+    bool kept = false;
+    for (uint32_t f : lf) kept = kept || (f & kKeptAtTransition);
+    if (!kept || r == max_rounds) break;
+    // back to u(T), which the limiter's first kernel of this step saved
+    CK(cudaMemcpy(c->u, c->u_old, size_t(c->M) * c->NS * sizeof(double) * C, cudaMemcpyDeviceToDevice),
+       "restore u(T)");
+    CK(cudaMemcpy(c->status, &status0, sizeof(uint32_t), cudaMemcpyHostToDevice), "reset status");
+    std::vector<uint8_t> troubled(C);
+    for (size_t i = 0; i < C; ++i) troubled[i] = (lf[i] & (kLimited | kKeptAtTransition)) ? 1 : 0;
+    std::vector<int8_t> fl(C);
+    c->tree.refine_around(troubled.data(), fl.data());
+    for (int8_t& f : fl) f = f > 0 ? 1 : 0;  // refinement only: nothing coarsens mid-step
+    st = ader_remesh(c, fl.data());
+    if (st != ADER_OK) return st;
+    st = ader_compute_dt(c, dt_dev, stream);
+    if (st != ADER_OK) return st;
+    ++r;
+  }
+  if (rounds) *rounds = r;
+  return ADER_OK;
+}
+
 ader_status ader_limiter_refine_flags(ader_ctx* c, int8_t* flags) {
   if (!c || !c->cfg.limiter || !flags) return ADER_ERR_ARG;
   const size_t C = c->tree.cells.size();

@@ -172,6 +172,12 @@ class Solver:
         """Remesh flags that refine around the last step's troubled cells."""
         return A.ader_limiter_refine_flags(self.ctx)
 
+    def step_refining(self, max_rounds=2, stream=None):
+        """One limited step; troubled cells at resolution transitions make the
+        context refine around them and redo the step from u(T).  Returns the
+        number of refinements."""
+        return A.ader_step_refining(self.ctx, self.dt, max_rounds, self._stream(stream))
+
     def force_limit(self, mask):
         """Treat the cells in ``mask`` as troubled in the following steps
         (None clears)."""

@@ -176,3 +176,54 @@ def test_refinement_follows_the_shock():
         perm = np.array([om.index[k] for k in keys])
         assert rel_l2(solver.get_state().cpu().numpy(), u[perm]) < TOL
     assert max(k[0] for k in om.cells) == 1
+
+
+def test_troubled_transition_cells_refine_and_redo():
+    """ader_step_refining: an explosion front crossing the transitions of a
+    refined patch; while troubled cells sit at a transition the step goes
+    back to u(T), refines around the troubled cells (refinement only) and
+    runs again.  The oracle takes the same steps (its limiter, its refine
+    flags without the coarsening, its transfer): rounds, meshes, flags and
+    states agree, and no troubled cell is left at a transition."""
+    from gpu_helpers import lib_keys
+    solver, om, perm = build_pair(2, 3, "euler", 27, 2, centers=[(0.5, 0.75)], radius=0.06,
+                                  limiter=True)
+    B = obasis.Basis(3)
+    P = opde.Euler(2)
+    X = om.node_coords(B.xi)
+    u = np.ascontiguousarray(np.moveaxis(workloads.circular_explosion(X, width=0.02), 0, 1))
+    solver.set_state(u[perm])
+    solver.compute_dt()
+    all_rounds = []
+    dt = oader.cfl_dt(u, om.cell_widths(), P, 3)
+    for cycle in range(2):
+        r = 0
+        while True:
+            ref = olim.step_limited(om, u, dt, P, B)
+            if not ref.kept.any() or r == 3:
+                break
+            fl = np.maximum(olim.refine_flags(om, ref.limited | ref.kept), 0).astype(np.int8)
+            u = om.remesh(u, fl, B)
+            dt = oader.cfl_dt(u, om.cell_widths(), P, 3)
+            r += 1
+        got_r = solver.step_refining(max_rounds=3)
+        assert got_r == r, (cycle, got_r, r)
+        all_rounds.append(r)
+        keys = lib_keys(solver)
+        assert sorted(keys) == om.cells
+        perm = np.array([om.index[k] for k in keys])
+        flags, nlim = solver.limiter_flags()
+        assert np.array_equal(flags, flags_of(ref)[perm])
+        assert rel_l2(solver.get_state().cpu().numpy(), ref.u[perm]) < TOL
+        assert abs(solver.dt.item() - ref.dt_next) < TOL * ref.dt_next
+        assert not ref.kept.any()
+        assert solver.status() == 0       # the discarded attempts' bits are dropped
+        u, dt = ref.u, ref.dt_next       # dt_next includes the limited cells' subcells
+    assert all_rounds[0] >= 2 and all_rounds[1] == 0
+    with pytest.raises(Exception):
+        from paper_1806_07984_gb300 import Solver
+        plain = Solver(2, 2, "euler", base=(3, 3, 1), cfl=0.1)
+        try:
+            plain.step_refining()
+        finally:
+            plain.close()
