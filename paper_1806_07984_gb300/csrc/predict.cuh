@@ -73,24 +73,45 @@ struct PredictSmem {
 enum TcMode { kTcNone = 0, kTcTF32 = 1, kTcTF32x3 = 2, kTcBF16x3 = 3 };
 
 // Shared memory and TMEM of the tensor-core path (one cell per CTA, 3D):
-// per direction d the derivative along d of all m n^2 lines is the product
-// A_d[lines x K] B_d[N x K]^T with A_d the slice's fluxes f_d laid out line
-// by line (K = the coordinate along d, padded to 8 TF32 / 16 BF16 values) and
-// B_d = D / h_d padded to 16 x K; lines are cut into M = 128 tiles.
+// per direction d the derivative along d of all m n^2 lines of CB time slices
+// at once is the product A_d[rows x K] B_d[N x K]^T with A_d the slices'
+// fluxes f_d laid out line by line, row (slice, variable, line) (K = the
+// coordinate along d, padded to 8 TF32 / 16 BF16 values), and B_d = D / h_d
+// padded to 16 x K; rows are cut into M = 128 tiles.  CB, the slices per MMA
+// chain: at n^3 <= 256 nodes two CTAs per SM hide the chain's latency better
+// than batching (measured at N = 5: TF32 61 ms per all-cell launch with one
+// slice per chain and two CTAs, 113 ms with all six slices and one CTA), so
+// CB = 1 there, the read-back in the predictor's own slice buffer; at larger
+// n one CTA per SM is all the registers allow and CB is the largest count
+// whose tiles fit 10 per direction (TMEM: 3 x 10 x 16 of 512 columns) and 128
+// KB of operands and whose read-back buffer G[CB][DIM][M][n^3] (FP32, aliased
+// onto the operand tiles once the MMAs have read them) is no larger than the
+// tiles (N = 7: TF32 205 ms with CB = 4, 255 ms with CB = 1).
 template <int DIM, int N, class PDE, int TC>
 struct TcLayout {
   static constexpr int n = N + 1;
-  static constexpr int ROWS = PDE::M * n * n;        // lines per direction
-  static constexpr int T = (ROWS + 127) / 128;       // M = 128 tiles per direction
+  static constexpr int NS = ipow(n, DIM);
+  static constexpr int ROWS1 = PDE::M * n * n;       // lines per direction and slice
   static constexpr int NSPLIT = TC == kTcTF32 ? 1 : 2;
   static constexpr int EB = TC == kTcBF16x3 ? 2 : 4; // operand element bytes
+  static constexpr int KPAD = 32 / EB;               // K per row (8 TF32, 16 BF16)
   static constexpr int KIND = TC == kTcBF16x3 ? 1 : 0;
-  static constexpr int A_BYTES = NSPLIT * DIM * T * tc::kTileBytes;
+  static constexpr int tiles(int cb) { return (cb * ROWS1 + 127) / 128; }
+  static constexpr int a_bytes(int cb) { return NSPLIT * DIM * tiles(cb) * tc::kTileBytes; }
+  static constexpr int g_bytes(int cb) { return cb * DIM * PDE::M * NS * 4; }
+  static constexpr int THREADS = (ipow(n, DIM) + 31) / 32 * 32;
+  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
+  static constexpr bool fits(int cb) {
+    return tiles(cb) <= 10 && a_bytes(cb) <= 128 * 1024 && g_bytes(cb) <= a_bytes(cb);
+  }
+  static constexpr int pick(int cb) { return cb <= 1 || fits(cb) ? cb : pick(cb - 1); }
+  static constexpr int CB = MIN_BLOCKS == 2 ? 1 : pick(n);
+  static constexpr int T = tiles(CB);                // M = 128 tiles per direction
+  static constexpr int A_BYTES = a_bytes(CB);
   static constexpr int B_BYTES = NSPLIT * DIM * 512;  // 16 rows x 32 bytes each
   static constexpr int COLS_USED = DIM * T * 16;
   static constexpr int COLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
                               : COLS_USED <= 256 ? 256 : 512;
-  static constexpr int THREADS = (ipow(n, DIM) + 31) / 32 * 32;
   __host__ __device__ static constexpr size_t bytes() { return size_t(A_BYTES + B_BYTES + 128); }
 };
 
@@ -229,8 +250,13 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     tc::fence_after();
   }
 
-  // g = sum_d (D/h_d)^(d) f_d(x) at this node, for the slice held in x.
-  auto divergence = [&](const Real(&x)[M], Real(&g)[M]) {
+  // ---- tensor-core contractions, up to L::CB time slices per MMA chain ----
+  // tc_put(j, x): the fluxes of slice x into rows (j, variable, line) of the
+  // operand tiles of every direction (hi/lo splits in the split modes); when
+  // the read-back aliases the tiles (CB > 1) the thread at line position 0
+  // also clears the row's K padding, which the previous chain's read-back may
+  // have overwritten.
+  auto tc_put = [&](int j, const Real(&x)[M]) {
     if constexpr (TC != kTcNone) {
       Real f[DIM][M];
       PDE::fluxes(x, f, gamma);
@@ -241,8 +267,9 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
           const int tl = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
 #pragma unroll
           for (int v = 0; v < M; ++v) {
-            const int r = v * n * n + tl;
-            const uint32_t o = (d * L::T + (r >> 7)) * tc::kTileBytes + tc::canon(r & 127, id[d] * L::EB);
+            const int r = (j * M + v) * n * n + tl;
+            const uint32_t t0 = (d * L::T + (r >> 7)) * tc::kTileBytes;
+            const uint32_t o = t0 + tc::canon(r & 127, id[d] * L::EB);
             const float val = float(f[d][v]);
             if constexpr (TC == kTcBF16x3) {
               const __nv_bfloat16 hi = __float2bfloat16_rn(val);
@@ -256,21 +283,43 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
             } else {
               *reinterpret_cast<float*>(tcA + o) = tc::to_tf32(val);
             }
+            if (L::CB > 1 && id[d] == 0) {
+#pragma unroll
+              for (int k = n; k < L::KPAD; ++k) {
+                const uint32_t oz = t0 + tc::canon(r & 127, k * L::EB);
+#pragma unroll
+                for (int h = 0; h < L::NSPLIT; ++h) {
+                  uint8_t* z = tcA + h * DIM * L::T * tc::kTileBytes + oz;
+                  if constexpr (L::EB == 2)
+                    *reinterpret_cast<uint16_t*>(z) = 0;
+                  else
+                    *reinterpret_cast<uint32_t*>(z) = 0u;
+                }
+              }
+            }
           }
         }
       }
+    }
+  };
+  // tc_run(cnt): the MMAs of cnt slices (one thread issues them and commits to
+  // the mbarrier; bounded wait), then the accumulators back into
+  // G[j][d][v][node] (FP32): the predictor's slice buffer when CB = 1, else
+  // the operand tiles, which the MMAs have finished reading.
+  auto tc_run = [&](int cnt) {
+    if constexpr (TC != kTcNone) {
       tc::fence_proxy_async();
       tc::fence_before();
       __syncthreads();
       tc::fence_after();
       const uint32_t taddr = tc_tmem;
+      const int tiles = (cnt * L::ROWS1 + 127) >> 7;
       if (tid == 0) {
         constexpr uint32_t ID = tc::idesc(L::KIND == 0 ? 2u : 1u, 128, 16);
         const uint32_t a0 = tc::smem_addr(tcA), b0 = tc::smem_addr(tcB);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-#pragma unroll
-          for (int t = 0; t < L::T; ++t) {
+          for (int t = 0; t < tiles; ++t) {
             const uint32_t dst = taddr + uint32_t((d * L::T + t) * 16);
             const uint32_t ahi = a0 + (d * L::T + t) * tc::kTileBytes;
             const uint32_t bhi = b0 + d * 512;
@@ -287,36 +336,48 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
       if (!tc::mbar_wait(&tc_mbar, tc_phase, 1 << 22)) atomicOr(status, kStatusTensorTimeout);
       tc_phase ^= 1u;
       tc::fence_after();
-      // read the accumulators back: warp w serves lane quarter w % 4
-      Real* G = my_fb;  // [DIM][M][NS]: derivative along d of f_d, per node
+      // warp w reads TMEM lane quarter w % 4
+      float* G = L::CB == 1 ? reinterpret_cast<float*>(my_fb) : reinterpret_cast<float*>(tcA);
       const int q = warp & 3;
       const int nwq = (int(blockDim.x >> 5) - q + 3) >> 2;
-      for (int job = warp >> 2; job < DIM * L::T; job += nwq) {
-        const int d = job / L::T, t = job % L::T;
+      for (int job = warp >> 2; job < DIM * tiles; job += nwq) {
+        const int d = job / tiles, t = job % tiles;
         float vals[8];
         tc::ld8(taddr + uint32_t((d * L::T + t) * 16) + (uint32_t(q * 32) << 16), vals);
         const int r = t * 128 + q * 32 + lane;
-        if (r < L::ROWS) {
-          const int v = r / (n * n), tl = r % (n * n);
+        if (r < cnt * L::ROWS1) {
+          const int j = r / L::ROWS1, rr = r - j * L::ROWS1;
+          const int v = rr / (n * n), tl = rr % (n * n);
 #pragma unroll
           for (int i = 0; i < n; ++i) {
             const int nd = d == 0 ? i + n * tl
                                   : (d == 1 ? (tl % n) + n * i + n * n * (tl / n) : tl + n * n * i);
-            G[(d * M + v) * NS + nd] = vals[i];
+            G[((j * DIM + d) * M + v) * NS + nd] = vals[i];
           }
         }
       }
       tc::fence_before();
       __syncthreads();
+    }
+  };
+  // tc_get(j, g): g = sum_d (D/h_d)^(d) f_d of slice j of the last chain at
+  // this node.  The caller synchronises before the next tc_put.
+  auto tc_get = [&](int j, Real(&g)[M]) {
+    if constexpr (TC != kTcNone) {
+      const float* G = L::CB == 1 ? reinterpret_cast<const float*>(my_fb)
+                                  : reinterpret_cast<const float*>(tcA);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         g[v] = Real(0);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) g[v] += active ? G[(d * M + v) * NS + node] : Real(0);
+        for (int d = 0; d < DIM; ++d) g[v] += active ? G[((j * DIM + d) * M + v) * NS + node] : Real(0);
       }
-      __syncthreads();
-      return;
     }
+  };
+
+  // g = sum_d (D/h_d)^(d) f_d(x) at this node, for the slice held in x
+  // (CUDA-core contraction over the slice's fluxes staged in shared memory).
+  auto divergence = [&](const Real(&x)[M], Real(&g)[M]) {
     Real f[DIM][M];
     PDE::fluxes(x, f, gamma);
     if (active) {
@@ -418,13 +479,55 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
     Real q[n][M];
     {
       Real g[M];
-      divergence(uu, g);
+      if constexpr (TC != kTcNone) {
+        tc_put(0, uu);
+        tc_run(1);
+        tc_get(0, g);
+        __syncthreads();
+      } else {
+        divergence(uu, g);
+      }
 #pragma unroll
       for (int k = 0; k < n; ++k)
 #pragma unroll
         for (int v = 0; v < M; ++v) q[k][v] = fma(sRs[k], g[v], uu[v]);
     }
-    for (int r = 1; r < iters; ++r) {
+    if constexpr (TC != kTcNone) {
+      // later iterations: the contractions of L::CB slices per MMA chain
+      // (their fluxes all come from the previous iterate)
+      for (int r = 1; r < iters; ++r) {
+        Real acc[n][M];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int v = 0; v < M; ++v) acc[k][v] = uu[v];
+#pragma unroll
+        for (int l0 = 0; l0 < n; l0 += L::CB) {
+#pragma unroll
+          for (int j = 0; j < L::CB; ++j)
+            if (l0 + j < n) tc_put(j, q[l0 + j]);
+          tc_run(l0 + L::CB <= n ? L::CB : n - l0);
+#pragma unroll
+          for (int j = 0; j < L::CB; ++j) {
+            if (l0 + j >= n) continue;
+            Real g[M];
+            tc_get(j, g);
+#pragma unroll
+            for (int k = 0; k < n; ++k) {
+              const Real c = sMd[k * n + l0 + j];
+#pragma unroll
+              for (int v = 0; v < M; ++v) acc[k][v] = fma(c, g[v], acc[k][v]);
+            }
+          }
+          __syncthreads();  // G is read: the next chain may overwrite the tiles
+        }
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int v = 0; v < M; ++v) q[k][v] = acc[k][v];
+      }
+    }
+    for (int r = 1; r < iters && TC == kTcNone; ++r) {
       Real acc[n][M];
 #pragma unroll
       for (int k = 0; k < n; ++k)
@@ -619,7 +722,7 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS,
 
 // Tensor-core predictor: one CTA (whole warps) per cell.
 template <int N, class PDE, int TC>
-__global__ void __launch_bounds__(TcLayout<3, N, PDE, TC>::THREADS)
+__global__ void __launch_bounds__(TcLayout<3, N, PDE, TC>::THREADS, TcLayout<3, N, PDE, TC>::MIN_BLOCKS)
     predict_tc_kernel(const PredictArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t slot = blockIdx.x;
