@@ -238,7 +238,7 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
         *reinterpret_cast<__nv_bfloat16*>(tcB + (DIM + d) * 512 + o) = lo;
       } else {
         const float hi = tc::to_tf32(float(x));
-        *reinterpret_cast<float*>(tcB + d * 512 + o) = TC == kTcTF32 ? float(x) : hi;
+        *reinterpret_cast<float*>(tcB + d * 512 + o) = hi;  // nearest TF32 (the MMA would truncate)
         if (TC == kTcTF32x3) *reinterpret_cast<float*>(tcB + (DIM + d) * 512 + o) = float(x - double(hi));
       }
     }
