@@ -10,6 +10,28 @@
 
 namespace ader {
 
+// 1 / x without an IEEE division: the hardware's approximate reciprocal
+// (PTX rcp.approx.ftz.f64) refined by two Newton-Raphson steps
+// y <- y + y (1 - x y), each of which doubles the number of correct bits
+// (Markstein, IBM J. Res. Dev. 34 (1990)).  Within a few units in the last
+// place for normal x; the Euler states that reach it have rho normal and
+// positive, and a zero, infinite or NaN rho gives a non-finite result that
+// the kernels' checks report.  FP32 keeps its division.
+__device__ __forceinline__ double recip(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+
+template <class R>
+__device__ __forceinline__ R recip_of(const R& x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ double recip_of<double>(const double& x) { return recip(x); }
+
 template <int DIM_>
 struct Euler {
   static constexpr int DIM = DIM_;
@@ -22,7 +44,7 @@ struct Euler {
   // All DIM fluxes at one node.
   template <class R>
   __device__ __forceinline__ static void fluxes(const R (&q)[M], R (&f)[DIM][M], R gamma) {
-    const R rinv = R(1) / q[0];
+    const R rinv = recip_of(q[0]);
     R v[DIM];
     R ke = R(0);
 #pragma unroll
@@ -49,7 +71,7 @@ struct Euler {
   // Flux in one direction d.
   template <class R>
   __device__ __forceinline__ static void flux(const R (&q)[M], int d, R (&f)[M], R gamma) {
-    const R rinv = R(1) / q[0];
+    const R rinv = recip_of(q[0]);
     R ke = R(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) ke = fma(q[1 + a], q[1 + a] * rinv, ke);
@@ -66,7 +88,7 @@ struct Euler {
   // physical (finite, rho > 0, p > 0).
   __device__ __forceinline__ static double max_speed(const double (&q)[M], int d, double gamma,
                                                      bool* ok) {
-    const double rinv = 1.0 / q[0];
+    const double rinv = recip(q[0]);
     double ke = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) ke = fma(q[1 + a], q[1 + a] * rinv, ke);

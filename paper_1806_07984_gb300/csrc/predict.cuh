@@ -662,34 +662,31 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
   }
 
   // id|dc: extrapolate Q-bar and the normal flux F-bar_d to the 2d faces.
+  // One face node per thread (2d n^(d-1) of them per cell, NS threads: all
+  // lanes busy, one pass at 3D N=5), each reading its line from shared memory;
+  // consecutive threads write consecutive face nodes.
+  for (int t = node; t < 2 * DIM * NF; t += NS) {
+    const int slot = t / NF, fnode = t - slot * NF;
+    const int d = slot >> 1, side = slot & 1;
+    const int ta = fnode % n, tb = fnode / n;  // tangential coordinates, lowest first
+    const int base = DIM == 2 ? (d == 0 ? n * ta : ta)
+                              : (d == 0 ? n * (ta + n * tb) : (d == 1 ? ta + n * n * tb : ta + n * tb));
+    const int sd = d == 0 ? 1 : (d == 1 ? n : n * n);
+    const Real* phi = side == 0 ? sp0 : sp1;
+    const int64_t fo = ((cell * 2 * DIM + slot) * M) * NF + fnode;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
+    for (int v = 0; v < M; ++v) {
+      const Real* lq = my_qs + v * NS + base;
+      const Real* lf = my_fb + (d * M + v) * NS + base;
+      const bool nz = PDE::flux_nonzero(d, v);
+      Real sq = Real(0), sf = Real(0);
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      if (id[d] != (side == 0 ? 0 : n - 1)) continue;
-      const Real* phi = side == 0 ? sp0 : sp1;
-      int fnode;
-      if (DIM == 2) {
-        fnode = d == 0 ? id[1] : id[0];
-      } else {
-        fnode = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
+      for (int j = 0; j < n; ++j) {
+        sq = fma(phi[j], lq[j * sd], sq);
+        if (nz) sf = fma(phi[j], lf[j * sd], sf);
       }
-      const int base = node - id[d] * stride[d];
-      const int64_t fo = ((cell * 2 * DIM + 2 * d + side) * M) * NF + fnode;
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        const Real* lq = my_qs + v * NS + base;
-        const Real* lf = my_fb + (d * M + v) * NS + base;
-        const bool nz = PDE::flux_nonzero(d, v);
-        Real sq = Real(0), sf = Real(0);
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          sq = fma(phi[j], lq[j * stride[d]], sq);
-          if (nz) sf = fma(phi[j], lf[j * stride[d]], sf);
-        }
-        faceQ[fo + v * NF] = double(sq);
-        faceF[fo + v * NF] = double(sf);
-      }
+      faceQ[fo + v * NF] = double(sq);
+      faceF[fo + v * NF] = double(sf);
     }
   }
 }
