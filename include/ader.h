@@ -229,6 +229,20 @@ ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_de
  * dt pointer recaptures.  If the capture fails the steps run eagerly. */
 ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
 
+/* One step with the state in host memory: u_in (host, [c][var][node], mesh
+ * order) is copied in and the new state copied out to u_out (host; may equal
+ * u_in), with *dt_dev read and the next dt written back as in ader_step.  The
+ * copy in runs on a stream of the context in contiguous cell ranges that end
+ * where the enclave pipeline's chunks start, and each enclave chunk's
+ * predictor waits only for its own range, so the copy overlaps the predictor;
+ * the skeleton predictor follows the last range; the copy out follows the
+ * corrector.  The result equals ader_set_state + ader_step + ader_get_state.
+ * Host buffers should be page-locked for the copies to overlap.  Ordered
+ * after earlier work on `stream`; the copy out is complete when later work on
+ * `stream` runs.  Not on a partitioned context or with the limiter. */
+ader_status ader_step_host(ader_ctx* ctx, const double* u_in, double* u_out, double* dt_dev,
+                           void* stream);
+
 /* Dynamic adaptivity (Sec. 2.3): flags per cell in mesh order (+1 refine,
  * -1 coarsen, 0 keep).  Refines flagged cells below max_level, restores 2:1
  * face balance by further refinement, coarsens complete families of flagged

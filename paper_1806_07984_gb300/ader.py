@@ -44,7 +44,8 @@ EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", 
            "ader_mesh_pipeline", "ader_partition", "ader_dd_info", "ader_dd_cuts",
            "ader_halo_size", "ader_halo_pack", "ader_halo_unpack", "ader_migrate_size",
            "ader_migrate_pack", "ader_migrate_unpack", "ader_mesh_partition",
-           "ader_mesh_subdomain", "ader_debug_fail_allocations", "ader_step_refining"]
+           "ader_mesh_subdomain", "ader_debug_fail_allocations", "ader_step_refining",
+           "ader_step_host"]
 ADER_DT_STATIC_MAX_CELLS = 1048576
 
 
@@ -142,6 +143,7 @@ def lib():
                                 ctypes.c_int),
         "ader_partition": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "ader_debug_fail_allocations": ([ctypes.c_int], ctypes.c_int),
+        "ader_step_host": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "ader_step_refining": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp], ctypes.c_int),
         "ader_dd_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _i64p, _i64p,
                           _i64p, _i64p], ctypes.c_int),
@@ -597,3 +599,9 @@ def ader_step_refining(ctx, dt, max_rounds, stream=None):
     _check(ctx, lib().ader_step_refining(ctx, _ptr(dt), max_rounds, ctypes.byref(r), stream),
            "ader_step_refining")
     return r.value
+
+
+def ader_step_host(ctx, u_in, u_out, dt, stream=None):
+    """One step with the state read from u_in and written to u_out (host
+    buffers, page-locked for the copies to overlap the predictor)."""
+    _check(ctx, lib().ader_step_host(ctx, _ptr(u_in), _ptr(u_out), _ptr(dt), stream), "ader_step_host")

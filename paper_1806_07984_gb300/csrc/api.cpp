@@ -37,6 +37,8 @@ struct ader_ctx {
   BasisTables B{};
   double inv_h[kMaxLevels][3]{};
   cudaStream_t s_hi = nullptr, s_lo = nullptr;
+  cudaStream_t s_copy = nullptr;          // host copies of ader_step_host (created on first use)
+  std::vector<cudaEvent_t> ev_copy;       // one per copied cell range
   cudaEvent_t ev_begin = nullptr, ev_step = nullptr, ev_lo = nullptr, ev_end = nullptr;
   // device buffers (capacity in cells)
   int64_t cap = 0;
@@ -631,8 +633,11 @@ void ader_destroy(ader_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : {c->ev_begin, c->ev_step, c->ev_lo, c->ev_end})
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_copy)
+    if (e) cudaEventDestroy(e);
   if (c->s_hi) cudaStreamDestroy(c->s_hi);
   if (c->s_lo) cudaStreamDestroy(c->s_lo);
+  if (c->s_copy) cudaStreamDestroy(c->s_copy);
   delete c;
 }
 
@@ -831,6 +836,101 @@ void capture_step(ader_ctx* c, double* dt_dev) {
     c->graph_dt = dt_dev;
   }
   if (g) cudaGraphDestroy(g);
+}
+
+// One step with the state read from and written to host memory.  The state
+// arrives in K contiguous cell ranges on a copy stream, range k ending where
+// enclave chunk k + 1 starts, so each enclave chunk's predictor waits only
+// for its own range and the copy of the next range overlaps it; the skeleton
+// predictor and the transition faces follow the last range; faces and
+// correctors then run as in step_pipelined, and the new state goes back in
+// one copy.  The order of the predictor tasks changes no result.
+ader_status step_host(ader_ctx* c, const double* u_in, double* u_out, double* dt_dev, cudaStream_t s) {
+  const MeshLists& t = *c->L;
+  const int K = std::max(1, t.chunks);
+  const int64_t C = t.nowned;
+  const size_t cell_bytes = size_t(c->M) * c->NS * sizeof(double);
+  if (!c->s_copy) CK(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking), "copy stream");
+  while (int(c->ev_copy.size()) < K) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    c->ev_copy.push_back(e);
+  }
+  while (int(c->ev_chunk.size()) < K) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    c->ev_chunk.push_back(e);
+  }
+  // cell ranges of the copies: range k = [start of enclave chunk k, start of
+  // enclave chunk k + 1), the first from cell 0, the last to the end
+  std::vector<int64_t> lo(size_t(K) + 1, C);
+  lo[0] = 0;
+  const int64_t ne = int64_t(t.encl_cells.size());
+  for (int k = 1; k < K; ++k) {
+    const int64_t p = t.chunk_off[size_t(k)];
+    lo[size_t(k)] = p < ne ? int64_t(t.encl_cells[size_t(p)]) : C;
+    lo[size_t(k)] = std::max(lo[size_t(k)], lo[size_t(k) - 1]);
+  }
+  CK(cudaEventRecord(c->ev_begin, s), "event");
+  CK(cudaStreamWaitEvent(c->s_copy, c->ev_begin, 0), "event");
+  for (int k = 0; k < K; ++k) {
+    const int64_t a = lo[size_t(k)], b = lo[size_t(k) + 1];
+    if (b > a)
+      CK(cudaMemcpyAsync(c->u + a * int64_t(c->M) * c->NS, u_in + a * int64_t(c->M) * c->NS,
+                         cell_bytes * size_t(b - a), cudaMemcpyHostToDevice, c->s_copy), "state in");
+    CK(cudaEventRecord(c->ev_copy[size_t(k)], c->s_copy), "event");
+  }
+  for (int k = 0; k < K; ++k) {
+    CK(cudaStreamWaitEvent(c->s_lo, c->ev_copy[size_t(k)], 0), "event");
+    PredictArgs pe = predict_args(c, dt_dev, ADER_ENCLAVE);
+    pe.cells = c->encl_cells + t.chunk_off[size_t(k)];
+    pe.count = t.chunk_off[size_t(k) + 1] - t.chunk_off[size_t(k)];
+    CK(do_predict(c, pe, c->s_lo), "enclave predictor");
+    CK(cudaEventRecord(c->ev_chunk[size_t(k)], c->s_lo), "event");
+  }
+  CK(cudaStreamWaitEvent(c->s_hi, c->ev_copy[size_t(K) - 1], 0), "event");
+  PredictArgs ps = predict_args(c, dt_dev, ADER_SKELETON);
+  CK(do_predict(c, ps, c->s_hi), "skeleton predictor");
+  ader_status st = enqueue_riemann(c, ADER_SKELETON, c->s_hi);
+  if (st != ADER_OK) return st;
+  const int cap = c->num_sms * (c->cfg.pipeline_ctas > 0 ? c->cfg.pipeline_ctas : 4);
+  auto correct_group = [&](int g) -> ader_status {
+    const int64_t b = t.corr_off[size_t(g)], e = t.corr_off[size_t(g) + 1];
+    if (e > b) {
+      CorrectArgs ca = stage_correct_args(c, dt_dev, c->corr_cells + b, e - b);
+      ca.max_ctas = cap;
+      CK(do_correct(c, true, ca, c->s_hi), "corrector");
+    }
+    return ADER_OK;
+  };
+  st = correct_group(0);
+  if (st != ADER_OK) return st;
+  for (int k = 0; k < K; ++k) {
+    CK(cudaStreamWaitEvent(c->s_hi, c->ev_chunk[size_t(k)], 0), "event");
+    RiemannArgs a = riemann_args(c);
+    a.conf = c->conf + t.n_conf_skeleton + t.face_off[size_t(k)];
+    a.nconf = t.face_off[size_t(k) + 1] - t.face_off[size_t(k)];
+    a.nparents = 0;
+    a.max_ctas = cap;
+    CK(do_faces(c, 0, a, c->s_hi), "riemann conforming faces");
+    st = correct_group(k + 1);
+    if (st != ADER_OK) return st;
+  }
+  st = enqueue_finish(c, dt_dev, dt_dev, c->s_hi);
+  if (st != ADER_OK) return st;
+  CK(cudaMemcpyAsync(u_out, c->u, cell_bytes * size_t(C), cudaMemcpyDeviceToHost, c->s_hi), "state out");
+  CK(cudaEventRecord(c->ev_end, c->s_hi), "event");
+  CK(cudaStreamWaitEvent(s, c->ev_end, 0), "event");
+  return ADER_OK;
+}
+
+ader_status ader_step_host(ader_ctx* c, const double* u_in, double* u_out, double* dt_dev, void* stream) {
+  if (!c || !u_in || !u_out || !dt_dev) return ADER_ERR_ARG;
+  if (c->partitioned || c->cfg.limiter || c->L->chunks < 1) {
+    c->err = "ader_step_host needs an unpartitioned context without the limiter";
+    return ADER_ERR_ARG;
+  }
+  return step_host(c, u_in, u_out, dt_dev, static_cast<cudaStream_t>(stream));
 }
 
 ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
