@@ -486,13 +486,20 @@ def run_batched(torch, precision, steps, warmup, count=512):
     launches = A.ader_batch_launch_count(b) - l0
     status = A.ader_batch_status_word(b)
     dofs = sum(s * s * 4 * (o + 1) ** 2 for s, o in zip(sides, orders))
+    flops = sum(predictor_flops_per_cell(2, o, o + 1, 4) * s * s for s, o in zip(sides, orders))
+    peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    achieved = flops * steps / el / 1e12
     A.ader_batch_destroy(b)
     return {"workload": f"{count} 2D Euler instances, sides 9..81, orders 3..7, seed 0",
             "precision": precision, "value": dofs * steps / el, "unit": "DoF-updates/s",
             "steps": steps, "ms_per_step": el / steps * 1e3, "dofs": dofs,
             "cells": sum(s * s for s in sides), "graph_launches": 1,
             "kernel_launches": launches, "tuned": {"ctas_per_sm": bps, "tile": tile,
-                                                   "step_ms": tune_ms}, "status": status}
+                                                   "step_ms": tune_ms}, "status": status,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "note": "predictor flops of every instance per step over the whole step's "
+                                 "time (faces and corrector included)"}}
 
 
 def run_adjoint(torch, predictor="picard"):
