@@ -162,14 +162,15 @@ class DistExchange:
         out = {q: torch.empty(int(n), dtype=torch.float64,
                               device="cpu" if self.host else like.device)
                for q, n in recv_sizes.items()}
-        reqs = []
-        for q in sorted(out):
-            reqs.append(self.dist.irecv(out[q], src=q, group=self.group))
-        for p in sorted(sends):
-            buf = sends[p].cpu() if self.host else sends[p]
-            reqs.append(self.dist.isend(buf, dst=p, group=self.group))
-        for r in reqs:
-            r.wait()
+        # one group of point-to-point operations: NCCL runs ungrouped sends and
+        # receives in issue order, which can deadlock when two ranks both
+        # receive first
+        ops = [self.dist.P2POp(self.dist.irecv, out[q], q, self.group) for q in sorted(out)]
+        ops += [self.dist.P2POp(self.dist.isend, sends[p].cpu() if self.host else sends[p], p,
+                                self.group) for p in sorted(sends)]
+        if ops:
+            for r in self.dist.batch_isend_irecv(ops):
+                r.wait()
         if self.host and like.is_cuda:
             out = {q: t.to(like.device) for q, t in out.items()}
         return out
