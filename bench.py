@@ -161,7 +161,8 @@ def step_roofline(prec, dim, order, m, ncells, step_s):
         terms["fp64_faces_corrector"] += pred / (FP64_PEAK_TFLOPS * 1e12)
         terms = {"hbm": terms["hbm"], "fp64_alu": terms["fp64_faces_corrector"]}
     elif prec == "df64":
-        terms["fp32_predictor"] = DF64_FP32_PER_FLOP * pred / 2 / (FP32_PEAK_TFLOPS * 1e12)
+        # FP32 instructions over the FP32 instruction rate (half the FMA-counted peak)
+        terms["fp32_predictor"] = DF64_FP32_PER_FLOP * pred / (FP32_PEAK_TFLOPS * 1e12 / 2)
     elif prec == "fp32":
         terms["fp32_predictor"] = pred / (FP32_PEAK_TFLOPS * 1e12)
     else:
