@@ -813,7 +813,10 @@ ader_status enqueue_step(ader_ctx* c, double* dt_dev) {
 }
 
 // Capture one step (both streams) into a CUDA graph for this mesh and dt
-// pointer.  On any capture failure the context keeps launching eagerly.
+// pointer.  The graph keeps each kernel's stream priority (without the
+// node-priority flag a replay runs every node at the launching stream's
+// priority, and the skeleton work would lose its precedence).  On any capture
+// failure the context keeps launching eagerly.
 void capture_step(ader_ctx* c, double* dt_dev) {
   drop_step_graph(c);
   const int64_t before = c->launches;
@@ -828,7 +831,7 @@ void capture_step(ader_ctx* c, double* dt_dev) {
   c->launches = before;
   cudaGetLastError();
   if (st != ADER_OK || e != cudaSuccess || !g ||
-      cudaGraphInstantiate(&c->step_exec, g, 0) != cudaSuccess) {
+      cudaGraphInstantiate(&c->step_exec, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     c->step_exec = nullptr;
     c->graphs_ok = false;
     cudaGetLastError();
