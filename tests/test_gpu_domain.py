@@ -11,22 +11,24 @@ from paper_1806_07984_gb300 import ader as A
 pytestmark = pytest.mark.gpu
 
 
-def _pair(dim, order, base, levels, center, radius, nranks, sigma=0.1):
+def _pair(dim, order, base, levels, center, radius, nranks, sigma=0.1, pde="euler",
+          precision="fp64", predictor="picard"):
     from paper_1806_07984_gb300 import Solver
     from paper_1806_07984_gb300.domain import LocalExchange, SubDomain
 
     def make():
-        s = Solver(dim, order, "euler", base=(base,) * 3, max_level=levels,
-                   cfl=workloads.ADER_CFL[order])
+        s = Solver(dim, order, pde, base=(base,) * 3, max_level=levels,
+                   cfl=workloads.ADER_CFL[order], precision=precision, predictor=predictor)
         for _ in range(levels):
             s.remesh(s.sphere_flags(center, radius))
         return s
 
     ref = make()
     X = ref.node_coords()
-    u = np.ascontiguousarray(np.moveaxis(
-        workloads.density_bubble(X, sigma=sigma, center=(0.5, 0.5, 0.5)[:dim],
-                                 vel=(1.0, 1.0, 1.0)[:dim]), 0, 1))
+    q = workloads.density_bubble(X, sigma=sigma, center=(0.5, 0.5, 0.5)[:dim],
+                                 vel=(1.0, 1.0, 1.0)[:dim]) if pde == "euler" else \
+        workloads.acoustic_pulses(X, seed=4, width=0.1)
+    u = np.ascontiguousarray(np.moveaxis(q, 0, 1))
     ref.set_state(u)
     ref.compute_dt()
     subs = []
@@ -43,12 +45,16 @@ def _gather(subs):
     return torch.cat([s.solver.get_state().reshape(-1) for s in subs])
 
 
-@pytest.mark.parametrize("dim,order,base,levels,nranks", [(2, 3, 9, 2, 3), (3, 3, 5, 1, 4),
-                                                          (2, 5, 9, 2, 2)])
-def test_subdomains_equal_whole_mesh_bitwise(dim, order, base, levels, nranks):
+@pytest.mark.parametrize("dim,order,base,levels,nranks,pde,precision,predictor", [
+    (2, 3, 9, 2, 3, "euler", "fp64", "picard"), (3, 3, 5, 1, 4, "euler", "fp64", "picard"),
+    (2, 5, 9, 2, 2, "euler", "fp64", "picard"), (3, 5, 5, 1, 3, "euler", "fp32", "picard"),
+    (2, 4, 9, 2, 3, "euler", "df64", "picard"), (3, 4, 5, 1, 3, "acoustics", "fp64", "ck")])
+def test_subdomains_equal_whole_mesh_bitwise(dim, order, base, levels, nranks, pde, precision,
+                                             predictor):
     from paper_1806_07984_gb300.domain import remesh_local, step_local
     center = (0.45, 0.5, 0.55)[:dim]
-    ref, subs, ex = _pair(dim, order, base, levels, center, 0.2, nranks)
+    ref, subs, ex = _pair(dim, order, base, levels, center, 0.2, nranks, pde=pde,
+                          precision=precision, predictor=predictor)
     info = [s.info() for s in subs]
     assert sum(i[4] for i in info) == ref.ncells
     assert all(i[5] > 0 for i in info)                     # every rank has ghosts
