@@ -503,6 +503,61 @@ def run_batched(torch, precision, steps, warmup, count=512):
                                  "time (faces and corrector included)"}}
 
 
+def run_dd_virtual(torch, nranks=4, steps=5, warmup=2):
+    """The bench mesh split into `nranks` sub-domains of the SFC partition on
+    one GPU (virtual ranks, device copies between their exchange buffers),
+    stepped together, against the same steps of the unpartitioned context
+    with the enclave pipeline off (the sub-domains run one chunk each): the
+    cost of the ghost faces, the halo packing and the exchange."""
+    from paper_1806_07984_gb300 import domain
+    global PIPELINE_CHUNKS
+    wl = WORKLOADS["euler3d-n5-amr"]
+    dev = torch.device("cuda", 0)
+    saved, PIPELINE_CHUNKS = PIPELINE_CHUNKS, 1
+    try:
+        ref, u0 = build_problem(wl, "fp64", dev)
+        subs = []
+        for r in range(nranks):
+            s, _ = build_problem(wl, "fp64", dev)
+            s.set_state(u0)
+            s.compute_dt()
+            subs.append(domain.SubDomain(s, nranks, r))
+    finally:
+        PIPELINE_CHUNKS = saved
+    ref.set_state(u0)
+    ref.compute_dt()
+    ex = domain.LocalExchange(subs)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ref.step(warmup)
+    torch.cuda.synchronize()
+    e0.record(st)
+    ref.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_ref = e0.elapsed_time(e1) / 1e3
+    domain.step_local(subs, ex, warmup)
+    torch.cuda.synchronize()
+    e0.record(st)
+    domain.step_local(subs, ex, steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_dd = e0.elapsed_time(e1) / 1e3
+    dofs = dofs_of(ref) * steps
+    info = [s.info() for s in subs]
+    out = {"workload": f"3D Euler N=5 bench mesh ({ref.ncells} cells), {nranks} sub-domains on one GPU, "
+                       f"{steps} steps after {warmup}",
+           "value": dofs / t_dd, "unit": "DoF-updates/s", "ms_per_step": t_dd / steps * 1e3,
+           "unpartitioned_ms_per_step": t_ref / steps * 1e3, "overhead": t_dd / t_ref - 1.0,
+           "owned_cells": [i[4] for i in info], "ghost_cells": [i[5] for i in info],
+           "halo_bytes_per_step": sum(s.halo_bytes() for s in subs),
+           "status": max(s.solver.status() for s in subs)}
+    for s in subs:
+        s.solver.close()
+    ref.close()
+    return out
+
+
 def run_adjoint(torch, predictor="picard"):
     """3D linear acoustics N=4 on 27^3 (FP64; Picard with 13 iterations or the
     Cauchy-Kowalevski predictor): one loss and gradient with respect to the
@@ -844,6 +899,8 @@ def summarise(line):
         out["n7"] = digest(cf["euler3d-n7-amr"])
     if "euler2d-n3-vortex" in cf:
         out["vortex_n3"] = digest({"fp64": cf["euler2d-n3-vortex"]})["fp64"]
+    if line.get("dd_virtual"):
+        out["dd4_overhead"] = _g(line["dd_virtual"]["overhead"])
     return out
 
 
@@ -863,10 +920,12 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-limiter", action="store_true")
     ap.add_argument("--no-ck", action="store_true")
-    ap.add_argument("--section", choices=["ck", "limiter", "adjoint", "batched"], default=None,
+    ap.add_argument("--section", choices=["ck", "limiter", "adjoint", "batched", "dd"], default=None,
                     help="run one side section alone and print its JSON object (no headline)")
     ap.add_argument("--ck-base", type=int, default=54, help="grid of the CK section (base^3)")
     ap.add_argument("--no-indicator", action="store_true")
+    ap.add_argument("--no-dd", action="store_true",
+                    help="skip the 4-sub-domain partitioned step on one GPU")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 2D N=3 vortex and 3D N=7 sections")
     ap.add_argument("--pipeline", type=int, default=0,
@@ -891,7 +950,8 @@ def main():
                "adjoint": lambda: {"picard": run_adjoint(torch, "picard"),
                                    "ck": run_adjoint(torch, "ck")},
                "batched": lambda: {"fp64": run_batched(torch, "fp64", 20, 2),
-                                   "fp32": run_batched(torch, "fp32", 20, 2)}}[args.section]()
+                                   "fp32": run_batched(torch, "fp32", 20, 2)},
+               "dd": lambda: run_dd_virtual(torch)}[args.section]()
         print(json.dumps({"section": args.section, args.section: out}))
         return
     rank, world, local = dist_env()
@@ -1081,6 +1141,7 @@ def main():
     limiter = ({"2d_n3_729": run_limiter(torch, 2, 3, 729), "3d_n5_27": run_limiter(torch, 3, 5, 27, 5)}
                if (not args.no_limiter and world == 1) else None)
     ck = run_ck(torch, base=args.ck_base) if (not args.no_ck and world == 1) else None
+    dd = run_dd_virtual(torch) if (not args.no_dd and world == 1) else None
 
 
     line = {"metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
@@ -1104,7 +1165,7 @@ def main():
                                "reclassification; the paper's timings exclude remeshing"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
             "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter,
-            "ck": ck, "indicator": indicator, "configs": configs}
+            "ck": ck, "indicator": indicator, "configs": configs, "dd_virtual": dd}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, seconds=10.0,
