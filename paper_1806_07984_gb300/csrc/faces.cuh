@@ -17,8 +17,9 @@
 // * transfer      - remesh volume transfer: copy, interpolate into a child,
 //                   or L2-project 3^d children onto the parent.
 // All in FP64.  Conforming faces: 32/G faces per warp for faces of at most 32
-// nodes (G lanes each), 128 / NF faces per 128-thread CTA for 36 or 49 nodes;
-// child faces: one warp per face (lanes over face nodes).
+// nodes (G lanes each), 8 faces per CTA for 36 or 49 nodes; child faces: in
+// 3D one CTA per parent face with separable prolongation, in 2D one warp per
+// child face (lanes over face nodes).
 #pragma once
 #include "kernels.h"
 #include "pde.cuh"
@@ -128,14 +129,14 @@ __global__ void riemann_conf_kernel(const RiemannArgs a) {
 // Faces whose node count is above 32 and not a multiple of 32 (3D, N = 5, 6):
 // one thread per face node, the speed of each face reduced with shared-memory
 // atomics on the FP64 bit pattern (non-negative values); no lane idles
-// across the two passes a warp per face would take.  Faces per CTA: as many as
-// fit in 128 threads, so that a CTA (about 7k registers) fits on an SM beside
-// two CTAs of the FP32 predictor (57k) and the face solves of the enclave
-// pipeline overlap the predictor instead of displacing it.
+// across the two passes a warp per face would take.  8 faces per CTA (288
+// threads at 36 nodes: whole warps, every lane busy; 3 faces in 128 threads,
+// small enough to sit beside two FP32 predictor CTAs, measured 1.2 % slower
+// on the FP32-predictor step).
 template <int NF>
 struct FaceBlock {
   static constexpr bool kUse = NF > 32 && NF % 32 != 0;
-  static constexpr int FPC = NF >= 128 ? 1 : 128 / NF;
+  static constexpr int FPC = 8;
   static constexpr int THREADS = (FPC * NF + 31) / 32 * 32;
 };
 
@@ -268,6 +269,95 @@ __global__ void riemann_child_kernel(const RiemannArgs a) {
       else
         rusanov_store<DIM, N, PDE>(Qf[t], Ff, Qv[t], Fv, smax, a.fstar + oF + fn, nullptr, NF);
     }
+  }
+}
+
+// 3D child faces, one CTA per parent face and one thread per child-face node
+// (3^2 child faces of n^2 nodes).  The coarse face's Q-bar and F-bar are
+// interpolated separably: first along the lower tangential axis for the three
+// sub-positions s0 into shared memory (T[s0][ia][j] = sum_i P[s0][ia][i]
+// X[i + n j]), then along the upper axis per child node (sum_j P[s1][ib][j]
+// T[s0][ia][j]) -- the summation order of prolong_node, so the values are the
+// same bit for bit, with about a fifth of its multiply-adds.  The speed of
+// each child face is reduced in shared memory (atomicMax on the FP64 bit
+// pattern of non-negative values).
+template <int N>
+struct ChildBlock {
+  static constexpr int n = N + 1, NF = n * n, S = 9;
+  static constexpr int THREADS = (S * NF + 31) / 32 * 32;
+};
+
+template <int DIM, int N, class PDE>
+__global__ void __launch_bounds__(ChildBlock<N>::THREADS) riemann_child_block_kernel(const RiemannArgs a) {
+  static_assert(DIM == 3, "3D child faces");
+  using CB = ChildBlock<N>;
+  constexpr int n = CB::n, NF = CB::NF, S = CB::S, M = PDE::M;
+  __shared__ double X[2][M][NF];         // coarse face: Q-bar, F-bar
+  __shared__ double T[3][2][M][n][n];    // after the lower tangential axis
+  __shared__ unsigned long long smax[S];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  for (int64_t p = blockIdx.x; p < a.nparents; p += gridDim.x) {
+    const ParentFace pf = a.parents[p];
+    const int d = pf.dir, cs = pf.coarse_side;
+    const int64_t oC = (int64_t(pf.coarse) * 2 * DIM + 2 * d + cs) * M * NF;
+    __syncthreads();  // the previous parent face is done with the shared buffers
+    for (int t = tid; t < 2 * M * NF; t += blockDim.x) {
+      const int qf = t / (M * NF), r = t - qf * M * NF;
+      X[qf][r / NF][r % NF] = (qf == 0 ? a.faceQ : a.faceF)[oC + r];
+    }
+    if (tid < S) smax[tid] = 0ull;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int t = tid; t < 3 * 2 * M * n * n; t += blockDim.x) {
+      const int j = t % n, ia = (t / n) % n, v = (t / (n * n)) % M, qf = (t / (n * n * M)) % 2,
+                s0 = t / (n * n * M * 2);
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < n; ++i) acc = fma(a.B.P[s0][ia][i], X[qf][v][i + n * j], acc);
+      T[s0][qf][v][ia][j] = acc;
+    }
+    __syncthreads();
+    const int sigma = tid / NF, fn = tid - sigma * NF;
+    const bool valid = sigma < S;
+    double Qv[M], Fv[M], Qf[M], Ff[M];
+    int64_t oF = 0;
+    if (valid) {
+      const int s0 = sigma % 3, s1 = sigma / 3, ia = fn % n, ib = fn / n;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        double q = 0.0, f = 0.0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          const double w = a.B.P[s1][ib][j];
+          q = fma(w, T[s0][0][v][ia][j], q);
+          f = fma(w, T[s0][1][v][ia][j], f);
+        }
+        Qv[v] = q;
+        Fv[v] = f;
+      }
+      const int64_t fine = a.child_fine[p * S + sigma];
+      oF = (fine * 2 * DIM + 2 * d + (1 - cs)) * M * NF;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        Qf[v] = a.faceQ[oF + v * NF + fn];
+        Ff[v] = a.faceF[oF + v * NF + fn];
+      }
+      bool o1, o2;
+      const double l = fmax(PDE::max_speed(Qv, d, a.gamma, &o1), PDE::max_speed(Qf, d, a.gamma, &o2));
+      if (l > 0.0)  // a NaN speed is left out, as fmax does
+        atomicMax(&smax[sigma], static_cast<unsigned long long>(__double_as_longlong(l)));
+      if (!(o1 && o2)) bad = 1;
+    }
+    __syncthreads();
+    if (valid) {
+      const double sp = __longlong_as_double(static_cast<long long>(smax[sigma]));
+      if (cs == 1)  // coarse cell on the left
+        rusanov_store<DIM, N, PDE>(Qv, Fv, Qf, Ff, sp, a.fstar + oF + fn, nullptr, NF);
+      else
+        rusanov_store<DIM, N, PDE>(Qf, Ff, Qv, Fv, sp, a.fstar + oF + fn, nullptr, NF);
+    }
+    if (tid == 0 && bad) atomicOr(a.status, kStatusNonPhysical);
   }
 }
 
@@ -595,9 +685,12 @@ cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
     riemann_conf_block_kernel<DIM, N, PDE><<<unsigned(b), FB::THREADS, 0, s>>>(a);
   } else if (which == 0)
     riemann_conf_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
-  else if (which == 1)
-    riemann_child_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
-  else
+  else if (which == 1) {
+    if constexpr (DIM == 3)
+      riemann_child_block_kernel<DIM, N, PDE><<<unsigned(a.nparents), ChildBlock<N>::THREADS, 0, s>>>(a);
+    else
+      riemann_child_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
+  } else
     restrict_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
   return cudaGetLastError();
 }
