@@ -372,7 +372,8 @@ ader_status enqueue_riemann(ader_ctx* c, ader_set set, cudaStream_t s) {
   const MeshLists& t = *c->L;
   if (set == ADER_ALL || set == ADER_SKELETON) {
     CK(do_faces(c, 1, a, s), "riemann child faces");
-    CK(do_faces(c, 2, a, s), "restriction");
+    if (c->cfg.dim == 2)  // in 3D the child-face kernel also restricts
+      CK(do_faces(c, 2, a, s), "restriction");
   }
   if (set == ADER_SKELETON) {
     a.conf = c->conf;

@@ -9,7 +9,7 @@
 //                   tangential interpolation P_s of the coarse face data.
 // * restrict      - accumulate-Riemann: parent F* = sum_sigma (R_s0 x R_s1)
 //                   F*_sigma, children summed in ascending sigma (no atomics,
-//                   deterministic).
+//                   deterministic); in 3D fused into the child-face kernel.
 // * correct       - u = u* + dt sum_d h_d^-1 [lift0_{i_d} F*_{d,-} -
 //                   lift1_{i_d} F*_{d,+}] with lift = phi / w, and the CFL
 //                   rate max sum_d lambda_d / h_d by warp shuffles and one
@@ -272,30 +272,39 @@ __global__ void riemann_child_kernel(const RiemannArgs a) {
   }
 }
 
-// 3D child faces, one CTA per parent face and one thread per child-face node
-// (3^2 child faces of n^2 nodes).  The coarse face's Q-bar and F-bar are
-// interpolated separably: first along the lower tangential axis for the three
-// sub-positions s0 into shared memory (T[s0][ia][j] = sum_i P[s0][ia][i]
-// X[i + n j]), then along the upper axis per child node (sum_j P[s1][ib][j]
-// T[s0][ia][j]) -- the summation order of prolong_node, so the values are the
-// same bit for bit, with about a fifth of its multiply-adds.  The speed of
-// each child face is reduced in shared memory (atomicMax on the FP64 bit
-// pattern of non-negative values).
-template <int N>
+// 3D child faces and the restriction, one CTA per parent face and one thread
+// per child-face node (3^2 child faces of n^2 nodes).  The coarse face's
+// Q-bar and F-bar are interpolated separably: first along the lower
+// tangential axis for the three sub-positions s0 (T[s0][ia][j] = sum_i
+// P[s0][ia][i] X[i + n j]), then along the upper axis per child node (sum_j
+// P[s1][ib][j] T[s0][ia][j]) -- the summation order of prolong_node, so the
+// values are the same bit for bit, with about a fifth of its multiply-adds.
+// The speed of each child face is reduced in shared memory (atomicMax on the
+// FP64 bit pattern of non-negative values).  The child fluxes F*_s then stay
+// in shared memory for the coarse slot's restriction sum_s R_s F*_s, taken
+// separably in restrict_kernel's order (children s in turn, for each the
+// lower axis first), so that it too is the same bit for bit.
+template <int N, int M>
 struct ChildBlock {
   static constexpr int n = N + 1, NF = n * n, S = 9;
   static constexpr int THREADS = (S * NF + 31) / 32 * 32;
+  // shared doubles: phase 1 X[2][M][NF] + T[3][2][M][n][n], phase 2 Fs[S][M][NF]
+  static constexpr int kPhase1 = 2 * M * NF + 6 * M * n * n, kPhase2 = S * M * NF;
+  static constexpr int kBuf = kPhase1 > kPhase2 ? kPhase1 : kPhase2;
 };
 
 template <int DIM, int N, class PDE>
-__global__ void __launch_bounds__(ChildBlock<N>::THREADS) riemann_child_block_kernel(const RiemannArgs a) {
+__global__ void __launch_bounds__(ChildBlock<N, PDE::M>::THREADS) riemann_child_block_kernel(const RiemannArgs a) {
   static_assert(DIM == 3, "3D child faces");
-  using CB = ChildBlock<N>;
+  using CB = ChildBlock<N, PDE::M>;
   constexpr int n = CB::n, NF = CB::NF, S = CB::S, M = PDE::M;
-  __shared__ double X[2][M][NF];         // coarse face: Q-bar, F-bar
-  __shared__ double T[3][2][M][n][n];    // after the lower tangential axis
+  __shared__ double buf[CB::kBuf];
+  __shared__ double T2[S][M][n][n];  // restriction after the lower tangential axis
   __shared__ unsigned long long smax[S];
   __shared__ int bad;
+  auto X = reinterpret_cast<double (*)[M][NF]>(buf);                      // [2][M][NF]
+  auto T = reinterpret_cast<double (*)[2][M][n][n]>(buf + 2 * M * NF);    // [3][2][M][n][n]
+  auto Fs = reinterpret_cast<double (*)[M][NF]>(buf);                     // [S][M][NF], after T
   const int tid = threadIdx.x;
   for (int64_t p = blockIdx.x; p < a.nparents; p += gridDim.x) {
     const ParentFace pf = a.parents[p];
@@ -349,15 +358,33 @@ __global__ void __launch_bounds__(ChildBlock<N>::THREADS) riemann_child_block_ke
         atomicMax(&smax[sigma], static_cast<unsigned long long>(__double_as_longlong(l)));
       if (!(o1 && o2)) bad = 1;
     }
-    __syncthreads();
+    __syncthreads();  // speeds complete; T is no longer read, Fs may overwrite it
     if (valid) {
       const double sp = __longlong_as_double(static_cast<long long>(smax[sigma]));
       if (cs == 1)  // coarse cell on the left
-        rusanov_store<DIM, N, PDE>(Qv, Fv, Qf, Ff, sp, a.fstar + oF + fn, nullptr, NF);
+        rusanov_store<DIM, N, PDE>(Qv, Fv, Qf, Ff, sp, a.fstar + oF + fn, &Fs[sigma][0][fn], NF);
       else
-        rusanov_store<DIM, N, PDE>(Qf, Ff, Qv, Fv, sp, a.fstar + oF + fn, nullptr, NF);
+        rusanov_store<DIM, N, PDE>(Qf, Ff, Qv, Fv, sp, a.fstar + oF + fn, &Fs[sigma][0][fn], NF);
     }
     if (tid == 0 && bad) atomicOr(a.status, kStatusNonPhysical);
+    __syncthreads();
+    for (int t = tid; t < S * M * n * n; t += blockDim.x) {
+      const int j = t % n, ia = (t / n) % n, v = (t / (n * n)) % M, sg = t / (n * n * M);
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < n; ++i) acc = fma(a.B.R[sg % 3][ia][i], Fs[sg][v][i + n * j], acc);
+      T2[sg][v][ia][j] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < M * NF; t += blockDim.x) {
+      const int v = t / NF, node = t - v * NF, ia = node % n, ib = node / n;
+      double acc = 0.0;
+      for (int sg = 0; sg < S; ++sg) {
+#pragma unroll
+        for (int j = 0; j < n; ++j) acc = fma(a.B.R[sg / 3][ib][j], T2[sg][v][ia][j], acc);
+      }
+      a.fstar[oC + t] = acc;
+    }
   }
 }
 
@@ -687,11 +714,12 @@ cudaError_t launch_faces_t(int which, const RiemannArgs& a, cudaStream_t s) {
     riemann_conf_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
   else if (which == 1) {
     if constexpr (DIM == 3)
-      riemann_child_block_kernel<DIM, N, PDE><<<unsigned(a.nparents), ChildBlock<N>::THREADS, 0, s>>>(a);
+      riemann_child_block_kernel<DIM, N, PDE><<<unsigned(a.nparents), ChildBlock<N, PDE::M>::THREADS, 0, s>>>(a);
     else
       riemann_child_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
-  } else
+  } else if constexpr (DIM == 2) {
     restrict_kernel<DIM, N, PDE><<<unsigned(blocks), threads, 0, s>>>(a);
+  }  // 3D: the child-face kernel has restricted already
   return cudaGetLastError();
 }
 
