@@ -558,6 +558,43 @@ def run_dd_virtual(torch, nranks=4, steps=5, warmup=2):
     return out
 
 
+def run_shifted(torch, precs=("fp64", "fp32", "df64"), steps=6, warmup=2):
+    """Global time stepping with a prescribed dt by the shifted task graph
+    (ader_step_fixed_dt: the corrector of step k runs as the prologue of the
+    predictor of step k + 1, nsteps + 1 cell passes per call) against
+    ader_step (CFL time step from every corrector, enclave pipeline, CUDA
+    graph) on the bench mesh, both over `steps` steps in one call."""
+    wl = WORKLOADS["euler3d-n5-amr"]
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    out = {"workload": "3D Euler N=5 bench mesh, %d steps in one call after %d" % (steps, warmup)}
+    for prec in precs:
+        s, u0 = build_problem(wl, prec, dev)
+        s.set_state(torch.from_numpy(u0).to(dev))
+        s.compute_dt()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        s.step(warmup)
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        s.step(steps)
+        ev[1].record(st)
+        dt_next = torch.zeros(1, dtype=torch.float64, device=dev)
+        s.step_fixed_dt(warmup, dt_next)        # dt: the last CFL step of the loop above
+        torch.cuda.synchronize()
+        ev[2].record(st)
+        s.step_fixed_dt(steps, dt_next)
+        ev[3].record(st)
+        torch.cuda.synchronize()
+        t_step = ev[0].elapsed_time(ev[1]) / steps
+        t_fix = ev[2].elapsed_time(ev[3]) / steps
+        dofs = dofs_of(s)
+        out[prec] = {"value": dofs / (t_fix / 1e3), "unit": "DoF-updates/s",
+                     "ms_per_step": t_fix, "ader_step_ms_per_step": t_step,
+                     "speedup_vs_ader_step": t_step / t_fix, "status": s.status()}
+        s.close()
+    return out
+
+
 def run_adjoint(torch, predictor="picard"):
     """3D linear acoustics N=4 on 27^3 (FP64; Picard with 13 iterations or the
     Cauchy-Kowalevski predictor): one loss and gradient with respect to the
@@ -901,6 +938,9 @@ def summarise(line):
         out["vortex_n3"] = digest({"fp64": cf["euler2d-n3-vortex"]})["fp64"]
     if line.get("dd_virtual"):
         out["dd4_overhead"] = _g(line["dd_virtual"]["overhead"])
+    if line.get("shifted_fixed_dt"):
+        out["shifted_x"] = {p: _g(e["speedup_vs_ader_step"]) for p, e in line["shifted_fixed_dt"].items()
+                            if isinstance(e, dict)}
     return out
 
 
@@ -920,12 +960,15 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-limiter", action="store_true")
     ap.add_argument("--no-ck", action="store_true")
-    ap.add_argument("--section", choices=["ck", "limiter", "adjoint", "batched", "dd"], default=None,
+    ap.add_argument("--section", choices=["ck", "limiter", "adjoint", "batched", "dd", "shifted"],
+                    default=None,
                     help="run one side section alone and print its JSON object (no headline)")
     ap.add_argument("--ck-base", type=int, default=54, help="grid of the CK section (base^3)")
     ap.add_argument("--no-indicator", action="store_true")
     ap.add_argument("--no-dd", action="store_true",
                     help="skip the 4-sub-domain partitioned step on one GPU")
+    ap.add_argument("--no-shifted", action="store_true",
+                    help="skip the prescribed-dt shifted-task-graph steps")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 2D N=3 vortex and 3D N=7 sections")
     ap.add_argument("--pipeline", type=int, default=0,
@@ -951,7 +994,8 @@ def main():
                                    "ck": run_adjoint(torch, "ck")},
                "batched": lambda: {"fp64": run_batched(torch, "fp64", 20, 2),
                                    "fp32": run_batched(torch, "fp32", 20, 2)},
-               "dd": lambda: run_dd_virtual(torch)}[args.section]()
+               "dd": lambda: run_dd_virtual(torch),
+               "shifted": lambda: run_shifted(torch)}[args.section]()
         print(json.dumps({"section": args.section, args.section: out}))
         return
     rank, world, local = dist_env()
@@ -1142,6 +1186,7 @@ def main():
                if (not args.no_limiter and world == 1) else None)
     ck = run_ck(torch, base=args.ck_base) if (not args.no_ck and world == 1) else None
     dd = run_dd_virtual(torch) if (not args.no_dd and world == 1) else None
+    shifted = run_shifted(torch) if (not args.no_shifted and world == 1) else None
 
 
     line = {"metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
@@ -1165,7 +1210,8 @@ def main():
                                "reclassification; the paper's timings exclude remeshing"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "status": status,
             "clocks": clk, "mixed": mixed, "batched": batched, "adjoint": adjoint, "limiter": limiter,
-            "ck": ck, "indicator": indicator, "configs": configs, "dd_virtual": dd}
+            "ck": ck, "indicator": indicator, "configs": configs, "dd_virtual": dd,
+            "shifted_fixed_dt": shifted}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, seconds=10.0,

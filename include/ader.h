@@ -229,6 +229,25 @@ ader_status ader_correct(ader_ctx* ctx, const double* dt_dev, double* dt_next_de
  * dt pointer recaptures.  If the capture fails the steps run eagerly. */
 ader_status ader_step(ader_ctx* ctx, int nsteps, double* dt_dev, void* stream);
 
+/* Global time stepping with a prescribed time step size (Sec. 3, the shifted
+ * task graph: when the admissible time step sizes are known, the pass that
+ * finishes step k also issues the predictor tasks of step k + 1).  nsteps
+ * steps of *dt_dev (device scalar, read only) on the whole mesh, on the
+ * context's high-priority stream: one predictor pass, then per step the face
+ * solves (prolongation, Rusanov, restriction) and one pass per cell that
+ * corrects the cell (Eq. (4)) and immediately starts its next predictor; the
+ * last step ends with the plain corrector and its CFL reduction, whose time
+ * step goes to *dt_next_dev (device; NULL discards it).  nsteps + 1 cell
+ * passes instead of 2 nsteps.  The state equals nsteps rounds of
+ * ader_predict, ader_riemann and ader_correct with the same dt bit for bit.
+ * The non-physical-state check of the corrector runs in the final corrector
+ * only; the predictor's non-finite check runs every step.  Ordered after
+ * earlier work on `stream`, and later work on `stream` sees the result.
+ * ADER_ERR_ARG for nsteps < 0, a NULL dt_dev, a partitioned context or the
+ * limiter; nsteps == 0 does nothing. */
+ader_status ader_step_fixed_dt(ader_ctx* ctx, int nsteps, const double* dt_dev, double* dt_next_dev,
+                               void* stream);
+
 /* One step with the state in host memory: u_in (host, [c][var][node], mesh
  * order) is copied in and the new state copied out to u_out (host; may equal
  * u_in), with *dt_dev read and the next dt written back as in ader_step.  The

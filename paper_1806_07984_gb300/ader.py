@@ -30,7 +30,7 @@ ADER_FIELD_U, ADER_FIELD_USTAR, ADER_FIELD_FACE_Q, ADER_FIELD_FACE_F, ADER_FIELD
 EXPORTS = ["ader_init", "ader_destroy", "ader_error_string", "ader_last_error", "ader_mesh_info",
            "ader_mesh_cells", "ader_mesh_skeleton", "ader_nodes", "ader_set_state",
            "ader_get_state", "ader_get_field", "ader_compute_dt", "ader_predict", "ader_riemann",
-           "ader_correct", "ader_step", "ader_remesh", "ader_classify", "ader_sphere_flags",
+           "ader_correct", "ader_step", "ader_step_fixed_dt", "ader_remesh", "ader_classify", "ader_sphere_flags",
            "ader_status_word", "ader_launch_count", "ader_mesh_create", "ader_mesh_destroy",
            "ader_mesh_adapt", "ader_mesh_sizes", "ader_mesh_leaves", "ader_mesh_faces",
            "ader_mesh_sphere_flags", "ader_compute_dt_static", "ader_batch_init",
@@ -102,6 +102,7 @@ def lib():
         "ader_riemann": ([_vp, ctypes.c_int, _vp], ctypes.c_int),
         "ader_correct": ([_vp, _vp, _vp, _vp], ctypes.c_int),
         "ader_step": ([_vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "ader_step_fixed_dt": ([_vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
         "ader_remesh": ([_vp, _vp], ctypes.c_int),
         "ader_classify": ([_vp, _vp], ctypes.c_int),
         "ader_sphere_flags": ([_vp, _vp, ctypes.c_double, _vp], ctypes.c_int),
@@ -257,6 +258,11 @@ def ader_correct(ctx, dt_dev, dt_next_dev, stream=None):
 
 def ader_step(ctx, nsteps, dt_dev, stream=None):
     _check(ctx, lib().ader_step(ctx, nsteps, _ptr(dt_dev), stream), "ader_step")
+
+
+def ader_step_fixed_dt(ctx, nsteps, dt_dev, dt_next_dev=None, stream=None):
+    _check(ctx, lib().ader_step_fixed_dt(ctx, nsteps, _ptr(dt_dev), _ptr(dt_next_dev), stream),
+           "ader_step_fixed_dt")
 
 
 def ader_remesh(ctx, flags):

@@ -985,6 +985,41 @@ ader_status ader_step(ader_ctx* c, int nsteps, double* dt_dev, void* stream) {
   return ADER_OK;
 }
 
+// Global time stepping with a prescribed dt (Sec. 3, the shifted task graph):
+// the corrector of step k and the predictor of step k + 1 are one task per
+// cell (the predictor kernel's corrector prologue), so nsteps steps take
+// nsteps + 1 passes over the cells instead of 2 nsteps.  The call starts
+// with a plain predictor and ends with a plain corrector, whose CFL time step
+// goes to dt_next_dev; the result equals nsteps rounds of ader_predict,
+// ader_riemann and ader_correct with the same dt, bit for bit.
+ader_status ader_step_fixed_dt(ader_ctx* c, int nsteps, const double* dt_dev, double* dt_next_dev,
+                               void* stream) {
+  if (!c || !dt_dev || nsteps < 0) return ADER_ERR_ARG;
+  if (c->partitioned || c->cfg.limiter) {
+    c->err = "ader_step_fixed_dt needs an unpartitioned context without the limiter";
+    return ADER_ERR_ARG;
+  }
+  if (nsteps == 0) return ADER_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaEventRecord(c->ev_begin, s), "event");
+  CK(cudaStreamWaitEvent(c->s_hi, c->ev_begin, 0), "event");
+  CK(do_predict(c, predict_args(c, dt_dev, ADER_ALL), c->s_hi), "predictor");
+  for (int k = 0; k < nsteps; ++k) {
+    ader_status st = enqueue_riemann(c, ADER_ALL, c->s_hi);
+    if (st != ADER_OK) return st;
+    if (k + 1 == nsteps) break;
+    PredictArgs a = predict_args(c, dt_dev, ADER_ALL);
+    a.corr_fstar = c->fstar;
+    a.corr_u = c->u;
+    CK(do_predict(c, a, c->s_hi), "corrector and next predictor");
+  }
+  ader_status st = enqueue_correct(c, dt_dev, dt_next_dev ? dt_next_dev : c->dt_scratch, c->s_hi);
+  if (st != ADER_OK) return st;
+  CK(cudaEventRecord(c->ev_end, c->s_hi), "event");
+  CK(cudaStreamWaitEvent(s, c->ev_end, 0), "event");
+  return ADER_OK;
+}
+
 ader_status ader_classify(ader_ctx* c, const int8_t* flags) {
   if (!c) return ADER_ERR_ARG;
   CK(cudaDeviceSynchronize(), "sync before classify");

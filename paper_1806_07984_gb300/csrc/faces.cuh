@@ -474,40 +474,6 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* out) 
   }
 }
 
-// Corrector at one node: q = u* + dt sum_d h_d^-1 [lift0_{i_d} F*_{d,-} -
-// lift1_{i_d} F*_{d,+}] (face lifting of the weak form, GL mass matrix).
-template <int DIM, int N, int M>
-__device__ __forceinline__ void lift_node(const double* ustar, const double* fstar, int64_t cell,
-                                          int node, const double* lift0, const double* lift1,
-                                          const double* inv_h, double dt, double* u_out,
-                                          double (&q)[M]) {
-  constexpr int n = N + 1, NS = ipow(n, DIM), NF = ipow(n, DIM - 1);
-  const int id[3] = {node % n, (node / n) % n, node / (n * n)};
-  double upd[M];
-#pragma unroll
-  for (int v = 0; v < M; ++v) upd[v] = 0.0;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    int fnode;
-    if (DIM == 2)
-      fnode = d == 0 ? id[1] : id[0];
-    else
-      fnode = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
-    const double* F0 = fstar + (cell * 2 * DIM + 2 * d + 0) * M * NF + fnode;
-    const double* F1 = fstar + (cell * 2 * DIM + 2 * d + 1) * M * NF + fnode;
-    const double l0 = lift0[id[d]] * inv_h[d];
-    const double l1 = lift1[id[d]] * inv_h[d];
-#pragma unroll
-    for (int v = 0; v < M; ++v) upd[v] = fma(l0, F0[v * NF], fma(-l1, F1[v * NF], upd[v]));
-  }
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    const int64_t gi = (cell * M + v) * NS + node;
-    q[v] = fma(dt, upd[v], ustar[gi]);
-    u_out[gi] = q[v];
-  }
-}
-
 // Corrector CTAs: 128 threads over the flat (cell, node) index, grid-stride.
 // A CTA (about 7k registers) fits beside two CTAs of the FP32 predictor, so
 // the correctors of the enclave pipeline run on the FP64 pipe next to them.

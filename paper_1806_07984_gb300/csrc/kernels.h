@@ -49,6 +49,13 @@ struct PredictArgs {
   uint32_t* status;
   double inv_h[kMaxLevels][3];
   BasisTables B;
+  // Shifted task graph (Sec. 3, global time stepping with a prescribed dt):
+  // when corr_fstar is set, every node is first corrected with the previous
+  // step's u* (in ustar) and F* (in corr_fstar), u = u* + dt lifting(F*),
+  // written to corr_u (the buffer u points to), and the predictor starts from
+  // that state.
+  const double* corr_fstar;
+  double* corr_u;
 };
 
 struct RiemannArgs {

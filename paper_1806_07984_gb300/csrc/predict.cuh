@@ -41,6 +41,40 @@ struct PredictShape {
   static constexpr int THREADS = CPB * NS;
 };
 
+// Corrector at one node: q = u* + dt sum_d h_d^-1 [lift0_{i_d} F*_{d,-} -
+// lift1_{i_d} F*_{d,+}] (face lifting of the weak form, GL mass matrix).
+template <int DIM, int N, int M>
+__device__ __forceinline__ void lift_node(const double* ustar, const double* fstar, int64_t cell,
+                                          int node, const double* lift0, const double* lift1,
+                                          const double* inv_h, double dt, double* u_out,
+                                          double (&q)[M]) {
+  constexpr int n = N + 1, NS = ipow(n, DIM), NF = ipow(n, DIM - 1);
+  const int id[3] = {node % n, (node / n) % n, node / (n * n)};
+  double upd[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) upd[v] = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    int fnode;
+    if (DIM == 2)
+      fnode = d == 0 ? id[1] : id[0];
+    else
+      fnode = d == 0 ? id[1] + n * id[2] : (d == 1 ? id[0] + n * id[2] : id[0] + n * id[1]);
+    const double* F0 = fstar + (cell * 2 * DIM + 2 * d + 0) * M * NF + fnode;
+    const double* F1 = fstar + (cell * 2 * DIM + 2 * d + 1) * M * NF + fnode;
+    const double l0 = lift0[id[d]] * inv_h[d];
+    const double l1 = lift1[id[d]] * inv_h[d];
+#pragma unroll
+    for (int v = 0; v < M; ++v) upd[v] = fma(l0, F0[v * NF], fma(-l1, F1[v * NF], upd[v]));
+  }
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    const int64_t gi = (cell * M + v) * NS + node;
+    q[v] = fma(dt, upd[v], ustar[gi]);
+    u_out[gi] = q[v];
+  }
+}
+
 // Contraction steps: a plain FMA in FP32/FP64; for double-float the
 // compensated accumulation (no renormalisation per term) followed by one
 // `settle` at the end of the sum.
@@ -693,9 +727,13 @@ __device__ __forceinline__ void predict_cells(const BasisTables& B, double dt, d
 
 // Resident CTAs per SM the register allocation must allow: the double-float
 // variant's long dependent chains need two CTAs to keep the FP32 pipes busy.
+// The FP64 variant at 216 nodes (3D N=5) also runs two CTAs per SM, so one
+// CTA's barrier waits are covered by the other's FP64 work: 128 registers
+// with a few spills, measured 1 % faster per step than one CTA at 174.
 template <class Real, int NS>
 struct PredictMinBlocks {
-  static constexpr int value = (!std::is_same<Real, double>::value && NS <= 216) ? 2 : 1;
+  static constexpr bool kFP64 = std::is_same<Real, double>::value;
+  static constexpr int value = (kFP64 ? (NS > 128 && NS <= 216) : NS <= 216) ? 2 : 1;
 };
 
 template <int DIM, int N, class PDE, class Real, int SCHEME = 0>
@@ -712,6 +750,11 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS,
   const int lv = valid ? int(a.level[cell]) : 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) ihd[d] = a.inv_h[lv][d];
+  if (a.corr_fstar && valid) {  // shifted task graph: the previous step's corrector first
+    double q[PDE::M];
+    lift_node<DIM, N, PDE::M>(a.ustar, a.corr_fstar, cell, int(threadIdx.x) - cl * S::NS, a.B.lift0,
+                              a.B.lift1, ihd, *a.dt, a.corr_u, q);
+  }
   predict_cells<DIM, N, PDE, Real, kTcNone, SCHEME>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u,
                                                     a.ustar, a.faceQ, a.faceF, cell, valid, ihd,
                                                     smem_raw);
@@ -729,6 +772,11 @@ __global__ void __launch_bounds__(TcLayout<3, N, PDE, TC>::THREADS, TcLayout<3, 
   const int lv = valid ? int(a.level[cell]) : 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) ihd[d] = a.inv_h[lv][d];
+  if (a.corr_fstar && valid && int(threadIdx.x) < ipow(N + 1, 3)) {  // shifted task graph
+    double q[PDE::M];
+    lift_node<3, N, PDE::M>(a.ustar, a.corr_fstar, cell, int(threadIdx.x), a.B.lift0, a.B.lift1, ihd,
+                            *a.dt, a.corr_u, q);
+  }
   predict_cells<3, N, PDE, float, TC>(a.B, *a.dt, a.gamma, a.iters, a.status, a.u, a.ustar,
                                       a.faceQ, a.faceF, cell, valid, ihd, smem_raw);
 }

@@ -136,6 +136,14 @@ class Solver:
     def step(self, nsteps=1, stream=None):
         A.ader_step(self.ctx, nsteps, self.dt.data_ptr(), self._stream(stream))
 
+    def step_fixed_dt(self, nsteps=1, dt_next=None, stream=None):
+        """nsteps steps with the prescribed dt in ``self.dt`` (the shifted
+        task graph: corrector and next predictor as one pass per cell); the
+        final state's CFL time step goes to ``dt_next`` (a device scalar)
+        when given."""
+        A.ader_step_fixed_dt(self.ctx, nsteps, self.dt.data_ptr(),
+                             None if dt_next is None else dt_next.data_ptr(), self._stream(stream))
+
     def remesh(self, flags):
         A.ader_remesh(self.ctx, flags)
 
