@@ -125,7 +125,9 @@ typedef struct {
                                 (orders 1..7, 2D and 3D); see ader_correct, ader_limiter_flags */
   double limiter_delta0;     /* relaxed maximum principle: delta = max(delta0, eps (max - min)); */
   double limiter_eps;        /* values <= 0 select delta0 = 1e-4, eps = 1e-3 */
-  int pipeline_chunks;       /* ader_step: enclave chunks K (0 selects 8, 1 disables); see ader_step */
+  int pipeline_chunks;       /* ader_step: enclave chunks K (1 disables; 0 selects 8, or fewer on
+                                small meshes: at least 8 predictor CTAs per SM per chunk, recomputed
+                                after every remesh); see ader_step */
   int pipeline_ctas;         /* CTAs per SM of the overlapping face/corrector kernels (0 selects 4) */
   int eager_steps;           /* 1: ader_step launches every kernel itself instead of replaying a
                                 CUDA graph of one step (captured once per mesh and dt pointer) */

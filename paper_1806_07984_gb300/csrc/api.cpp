@@ -234,8 +234,22 @@ void drop_step_graph(ader_ctx* c) {
 }
 
 // Upload levels, cell lists and face lists of the current tree (synchronous).
+// Default enclave pipeline (cfg.pipeline_chunks == 0): 8 chunks, fewer when
+// the enclave holds less than 8 predictor CTAs per SM per chunk, down to one
+// chunk (no pipeline) for small meshes, whose steps are bound by the chain of
+// short launches rather than by the predictor.
+void fit_chunks(ader_ctx* c) {
+  if (c->partitioned || c->cfg.pipeline_chunks != 0) return;
+  const int64_t ns = ipow64(c->cfg.order + 1, c->cfg.dim);
+  const int64_t cpb = ns >= 128 ? 1 : 256 / ns;  // cells per predictor CTA
+  const int64_t ctas = (int64_t(c->tree.encl_cells.size()) + cpb - 1) / cpb;
+  const int k = int(std::max<int64_t>(1, std::min<int64_t>(8, ctas / (8 * int64_t(std::max(1, c->num_sms))))));
+  if (k != c->tree.chunks) c->tree.set_chunks(k);
+}
+
 ader_status upload_mesh(ader_ctx* c) {
   drop_step_graph(c);
+  fit_chunks(c);
   const MeshLists& t = *c->L;
   const int64_t C = t.nlocal;
   ader_status st = ensure_cells(c, C);

@@ -227,3 +227,40 @@ def test_troubled_transition_cells_refine_and_redo():
             plain.step_refining()
         finally:
             plain.close()
+
+
+def test_default_chunks_follow_the_mesh_size():
+    """pipeline_chunks = 0 keeps the pipeline off on a small mesh (729 cells:
+    fewer launches per step than 8 explicit chunks, the same state bit for
+    bit) and turns it on when remeshing makes the enclave large enough (the
+    27^2 base refined everywhere twice: 59,049 cells, 3,691 predictor CTAs of
+    16 cells, 8 CTAs per SM per chunk)."""
+    from paper_1806_07984_gb300 import Solver
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_step, states = {}, {}
+    for K in (0, 8, 1):
+        s = Solver(2, 3, "euler", base=(27, 27, 1), max_level=2, cfl=workloads.ADER_CFL[3],
+                   pipeline_chunks=K, eager_steps=True)
+        X = s.node_coords()
+        u0 = np.ascontiguousarray(np.moveaxis(workloads.isentropic_vortex(X[0], X[1]), 0, 1))
+        s.set_state(torch.from_numpy(u0).cuda())
+        s.compute_dt()
+        n0 = s.launch_count()
+        s.step(2)
+        per_step[K] = (s.launch_count() - n0) / 2
+        states[K] = (s.get_state().cpu().numpy(), s.dt.item())
+        if K == 0:
+            for _ in range(2):
+                s.remesh(np.ones(s.ncells, dtype=np.int8))
+            assert s.ncells == 59049
+            n0 = s.launch_count()
+            s.step(1)
+            big = s.launch_count() - n0
+            assert s.status() == 0
+        s.close()
+    assert per_step[0] == per_step[1] < per_step[8]
+    assert np.array_equal(states[0][0], states[8][0]) and states[0][1] == states[8][1]
+    assert np.array_equal(states[0][0], states[1][0])
+    k_big = max(1, min(8, ((59049 + 15) // 16) // (8 * sms)))
+    assert (big > per_step[1]) == (k_big > 1)
