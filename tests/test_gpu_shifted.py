@@ -111,3 +111,36 @@ def test_shifted_steps_reject_limiter_and_negative_counts():
     with pytest.raises(A.AderError):
         s.step_fixed_dt(-1)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_shifted_steps_full_size(precision):
+    """The 3D N=5 bench mesh (base 27^3, two levels around the bubble,
+    268,087 cells): two shifted steps equal two staged steps bit for bit."""
+    import torch
+    from paper_1806_07984_gb300 import Solver
+    runs = []
+    for shifted in (False, True):
+        s = Solver(3, 5, "euler", base=(27, 27, 27), max_level=2, cfl=workloads.ADER_CFL[5],
+                   precision=precision)
+        center = workloads.sphere_center(0.0)
+        for _ in range(2):
+            s.remesh(s.sphere_flags(center, 0.15))
+        s.classify(s.sphere_flags(center, 0.15))
+        assert s.ncells == 268087
+        X = s.node_coords()
+        s.set_state(torch.from_numpy(np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X), 0, 1))).cuda())
+        del X
+        s.compute_dt()
+        dt_next = torch.zeros(1, dtype=torch.float64, device=s.device)
+        if shifted:
+            s.step_fixed_dt(2, dt_next)
+        else:
+            for _ in range(2):
+                s.predict()
+                s.riemann()
+                s.correct(dt_next)
+        runs.append((s.get_state().cpu().numpy(), dt_next.item(), s.status()))
+        s.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1] and runs[0][2] == runs[1][2] == 0
