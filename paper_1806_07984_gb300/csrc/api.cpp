@@ -1160,10 +1160,10 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   // The mesh before the call: restored, with its device lists, when the
   // device side cannot follow (every buffer is allocated before an old one is
   // released, so u still holds the old state then).
-  Tree saved = c->tree;
+  Tree::State saved = c->tree.save();
   if (!c->tree.remesh(flags, &plan, &kids)) {
     c->err = c->tree.error();
-    c->tree = std::move(saved);
+    c->tree.restore(std::move(saved));
     return ADER_ERR_MESH;
   }
   const int64_t C_new = int64_t(c->tree.cells.size());
@@ -1173,7 +1173,7 @@ ader_status ader_remesh(ader_ctx* c, const int8_t* flags) {
   auto undo = [&](ader_status st) {
     const std::string why = c->err;
     if (own_old) cudaFree(old_u);
-    c->tree = std::move(saved);
+    c->tree.restore(std::move(saved));
     upload_mesh(c);  // the old mesh's lists fit the capacities already there
     c->err = why;
     return st;

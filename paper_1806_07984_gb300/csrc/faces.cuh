@@ -513,8 +513,9 @@ __global__ void __launch_bounds__(kCorrectThreads) correct_kernel(const CorrectA
   block_max_to(rate, a.rate_max);
 }
 
-// Remesh transfer: one CTA per new cell, threads over the nodes, separable
-// per-axis application of P_s (refine) or R_s (coarsen) in shared memory.
+// Remesh transfer: one CTA per new cell, threads over the nodes.  A kept cell
+// is copied; a refined or coarsened one gets the separable per-axis
+// application of P_s (refine) or R_s (coarsen) in shared memory.
 template <int DIM, int N, int M>
 __global__ void __launch_bounds__(PredictShape<DIM, N>::NS) transfer_kernel(const TransferArgs a) {
   constexpr int n = N + 1, NS = ipow(n, DIM);
@@ -523,6 +524,16 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::NS) transfer_kernel(cons
   if (c >= a.ncells_new) return;
   const TransferItem it = a.plan[c];
   const int node = threadIdx.x;
+  if (it.kind == 0) {  // a kept cell (most of them): a coalesced copy, no staging
+    int64_t src = int64_t(it.src);
+    if (src < 0 || src >= a.ncells_old) {
+      if (node == 0) atomicOr(a.status, kStatusBadTransfer);
+      src = 0;
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) a.u_new[(c * M + v) * NS + node] = a.u_old[(src * M + v) * NS + node];
+    return;  // the whole CTA (kind is uniform per cell)
+  }
   const int id[3] = {node % n, (node / n) % n, node / (n * n)};
   const int stride[3] = {1, n, n * n};
   double acc[M];

@@ -279,25 +279,50 @@ void Tree::classify(const int8_t* refine_flags) {
   std::vector<int> ready(chunk_of);
   const size_t nf = conf_all.size();
   std::vector<int> group(nf);  // -1: both cells skeleton, else the face's chunk
-  std::vector<int64_t> count(size_t(K) + 1, 0);
-  for (size_t f = 0; f < nf; ++f) {
-    const ConfFace& F = conf_all[f];
-    const int r = std::max(chunk_of[size_t(F.left)], chunk_of[size_t(F.right)]);
-    group[f] = r;
-    ++count[size_t(r + 1)];
-    if (r >= 0) {
-      ready[size_t(F.left)] = std::max(ready[size_t(F.left)], r);
-      ready[size_t(F.right)] = std::max(ready[size_t(F.right)], r);
+  // Faces in T contiguous ranges: groups, per-range counts, and each cell's
+  // latest face chunk (a maximum, so the order of the updates does not
+  // matter); then every range scatters its faces from its own offset in each
+  // group, which keeps conf_all order within a group as a sequential pass.
+  const int T = pass_threads(int64_t(nf));
+  std::vector<std::vector<int64_t>> cnt(size_t(T), std::vector<int64_t>(size_t(K) + 1, 0));
+  auto raise = [](int* p, int r) {
+    int cur = __atomic_load_n(p, __ATOMIC_RELAXED);
+    while (cur < r && !__atomic_compare_exchange_n(p, &cur, r, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
     }
-  }
+  };
+  parallel_ranges(int64_t(nf), T, [&](int t, int64_t b, int64_t e) {
+    std::vector<int64_t>& C = cnt[size_t(t)];
+    for (int64_t f = b; f < e; ++f) {
+      const ConfFace& F = conf_all[size_t(f)];
+      const int r = std::max(chunk_of[size_t(F.left)], chunk_of[size_t(F.right)]);
+      group[size_t(f)] = r;
+      ++C[size_t(r + 1)];
+      if (r >= 0) {
+        raise(&ready[size_t(F.left)], r);
+        raise(&ready[size_t(F.right)], r);
+      }
+    }
+  });
+  std::vector<int64_t> count(size_t(K) + 1, 0);
+  for (int t = 0; t < T; ++t)
+    for (int g = 0; g <= K; ++g) count[size_t(g)] += cnt[size_t(t)][size_t(g)];
   n_conf_skeleton = count[0];
   face_off.assign(size_t(K) + 1, 0);
   for (int k = 0; k < K; ++k) face_off[size_t(k) + 1] = face_off[size_t(k)] + count[size_t(k) + 1];
   std::vector<int64_t> put(size_t(K) + 1);
   put[0] = 0;
   for (int k = 0; k < K; ++k) put[size_t(k) + 1] = n_conf_skeleton + face_off[size_t(k)];
+  for (int t = 0; t < T; ++t)  // cnt[t] becomes range t's first slot in each group
+    for (int g = 0; g <= K; ++g) {
+      const int64_t c = cnt[size_t(t)][size_t(g)];
+      cnt[size_t(t)][size_t(g)] = put[size_t(g)];
+      put[size_t(g)] += c;
+    }
   conf.resize(nf);
-  for (size_t f = 0; f < nf; ++f) conf[size_t(put[size_t(group[f] + 1)]++)] = conf_all[f];
+  parallel_ranges(int64_t(nf), T, [&](int t, int64_t b, int64_t e) {
+    std::vector<int64_t>& at = cnt[size_t(t)];
+    for (int64_t f = b; f < e; ++f) conf[size_t(at[size_t(group[size_t(f)] + 1)]++)] = conf_all[size_t(f)];
+  });
   corr_off.assign(size_t(K) + 2, 0);
   for (size_t i = 0; i < n; ++i) ++corr_off[size_t(ready[i] + 1) + 1];
   for (int g = 0; g <= K; ++g) corr_off[size_t(g) + 1] += corr_off[size_t(g)];
@@ -326,6 +351,27 @@ void Tree::refine_around(const uint8_t* troubled, int8_t* flags) const {
     const int lv = cells[i].level;
     flags[i] = mark[i] ? (lv < max_level_ ? 1 : 0) : (lv > 0 ? -1 : 0);
   }
+}
+
+Tree::State Tree::save() const {
+  State s{cells, std::vector<int8_t>(cells.size(), 0), chunks};
+  for (size_t i = 0; i < cells.size(); ++i) s.refine_flags[i] = (skeleton[i] && !transition[i]) ? 1 : 0;
+  return s;
+}
+
+void Tree::restore(State&& s) {
+  leaves_.reset(s.leaves.size());
+  refined_.reset(s.leaves.size() / 8 + 16);
+  for (const Key& k : s.leaves) {
+    leaves_.insert(pack(k));
+    for (Key p = k; p.level > 0;) {  // ancestors up to the first one already known
+      p = parent(p);
+      if (!refined_.insert(pack(p))) break;
+    }
+  }
+  chunks = s.chunks;
+  build();
+  classify(s.refine_flags.data());
 }
 
 void Tree::set_chunks(int K) {

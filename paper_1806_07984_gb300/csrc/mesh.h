@@ -206,6 +206,20 @@ class Tree : public MeshLists {
 
   const std::string& error() const { return error_; }
 
+  // The adaptive state of the tree: its leaves, the refine flags of its
+  // split and the chunk count.  The refined set (the leaves' ancestors) and
+  // every list follow from it, so it is a much cheaper undo point than a copy
+  // of the whole tree.
+  struct State {
+    std::vector<Key> leaves;
+    std::vector<int8_t> refine_flags;
+    int chunks = 1;
+  };
+  State save() const;
+  // Back to a saved state of a balanced mesh: the leaf and refined sets, then
+  // build() and the split.
+  void restore(State&& s);
+
  private:
   bool is_leaf(const Key& k) const { return leaves_.count(pack(k)) != 0; }
   bool is_refined(const Key& k) const { return refined_.count(pack(k)) != 0; }
