@@ -357,10 +357,11 @@ def run_steps_dd(sub, ex, wl, k, t_dev, step_base):
     return dofs
 
 
-def l2_error_vs_exact(s, u_dev, t, init="bubble"):
+def l2_error_vs_exact(s, u_dev, t, init="bubble", maxes=None):
     """Per-variable L2 error (GL quadrature) of the state against the exact
     solution at time t (the translated bubble or vortex), relative to the L2
-    norm of the exact state."""
+    norm of the exact state; with a list `maxes`, also the per-variable
+    nodal max error relative to the exact state's max (appended to it)."""
     import torch
     X = s.node_coords()
     q = workloads.density_bubble(X, t=t) if init == "bubble" else \
@@ -383,6 +384,8 @@ def l2_error_vs_exact(s, u_dev, t, init="bubble"):
         nrm = (ex[:, v] ** 2 * W).reshape(len(cells), -1).sum(axis=1)
         errs.append(float(np.sqrt((e * vol).sum())))
         norms.append(float(np.sqrt((nrm * vol).sum())))
+        if maxes is not None:
+            maxes.append(float(np.abs(got[:, v] - ex[:, v]).max() / np.abs(ex[:, v]).max()))
     del xi
     return [e / nv for e, nv in zip(errs, norms)], got
 
@@ -416,10 +419,12 @@ def precision_sweep(torch, wl, precs, steps, warmup, device, base=None):
         f1.record(stream)
         torch.cuda.synchronize()
         el_m = f0.elapsed_time(f1) / 1e3
-        err_m, state_m = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()), wl["init"])
+        mx_m = []
+        err_m, state_m = l2_error_vs_exact(sm_, sm_.get_state(), float(t_m.item()), wl["init"], mx_m)
         value = dofs_m / el_m
         entry = {"value": value, "unit": "DoF-updates/s", "ms_per_step": el_m / steps * 1e3,
-                 "l2_rel_err_vs_exact": dict(zip(names, err_m)), "status": sm_.status()}
+                 "l2_rel_err_vs_exact": dict(zip(names, err_m)),
+                 "max_rel_err_vs_exact": dict(zip(names, mx_m)), "status": sm_.status()}
         if prec == "fp64" and base is None:
             base = (value, state_m, sm_.cells())
         else:
@@ -931,6 +936,21 @@ def summarise(line):
     if line.get("mixed"):
         out["n5"] = digest(line["mixed"])
         out["fp64_step_frac"] = out["n5"].get("fp64", {}).get("frac")
+        # per precision, per variable (in `vars` order): relative L2 and max
+        # error against the exact solution and against the FP64 result
+        names = None
+        per = {}
+        for prec, e in line["mixed"].items():
+            if not isinstance(e, dict) or "l2_rel_err_vs_exact" not in e:
+                continue
+            names = list(e["l2_rel_err_vs_exact"])
+            vs = e.get("vs_fp64_per_var", {})
+            per[prec] = {"x": _g(e.get("speedup_vs_fp64", 1.0), 3),
+                         "exact_l2": [_g(e["l2_rel_err_vs_exact"][v], 2) for v in names],
+                         "exact_max": [_g(e.get("max_rel_err_vs_exact", {}).get(v), 2) for v in names],
+                         "vs64_l2": [_g(vs.get(v, {}).get("rel_l2"), 2) for v in names] if vs else None,
+                         "vs64_max": [_g(vs.get(v, {}).get("rel_max"), 2) for v in names] if vs else None}
+        out["mixed_summary"] = {"vars": names, **per}
     cf = line.get("configs") or {}
     if "euler3d-n7-amr" in cf:
         out["n7"] = digest(cf["euler3d-n7-amr"])
@@ -941,6 +961,8 @@ def summarise(line):
     if line.get("shifted_fixed_dt"):
         out["shifted_x"] = {p: _g(e["speedup_vs_ader_step"]) for p, e in line["shifted_fixed_dt"].items()
                             if isinstance(e, dict)}
+    if "mixed_summary" in out:  # last, so that it ends the line
+        out["mixed_summary"] = out.pop("mixed_summary")
     return out
 
 
@@ -1140,7 +1162,8 @@ def main():
     # ---- mixed precision: FP32 / tensor-core predictors on the same workload ----
     mixed = None
     if args.precision == "fp64" and args.mixed and world == 1:
-        err64, state64 = l2_error_vs_exact(s, s.get_state(), float(t_dev.item()), wl["init"])
+        mx64 = []
+        err64, state64 = l2_error_vs_exact(s, s.get_state(), float(t_dev.item()), wl["init"], mx64)
         cells64 = s.cells()
         s.close()
         del u_dev
@@ -1148,6 +1171,7 @@ def main():
         mixed, _ = precision_sweep(torch, wl, args.mixed.split(","), args.steps, args.warmup,
                                    device, base=(value, state64, cells64))
         mixed["fp64"] = {"value": value, "l2_rel_err_vs_exact": dict(zip(names, err64)),
+                         "max_rel_err_vs_exact": dict(zip(names, mx64)),
                          "step_roofline": step_roofline("fp64", wl["dim"], wl["order"],
                                                         len(names), ncells,
                                                         elapsed / args.steps)}
