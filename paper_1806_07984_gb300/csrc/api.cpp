@@ -346,6 +346,7 @@ PredictArgs predict_args(ader_ctx* c, const double* dt, ader_set set) {
   a.gamma = c->cfg.gamma;
   a.iters = c->cfg.picard_iters > 0 ? c->cfg.picard_iters : c->cfg.order + 1;
   a.status = stage_status(c);
+  a.min_ctas = 2 * c->num_sms;
   std::memcpy(a.inv_h, c->inv_h, sizeof(a.inv_h));
   a.B = c->B;
   return a;

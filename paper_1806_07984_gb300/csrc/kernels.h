@@ -56,6 +56,9 @@ struct PredictArgs {
   // that state.
   const double* corr_fstar;
   double* corr_u;
+  // 0, or a CTA count: a launch that would have fewer CTAs with CPB cells
+  // each takes fewer cells per CTA (small meshes spread over more SMs).
+  int32_t min_ctas;
 };
 
 struct RiemannArgs {

@@ -149,9 +149,10 @@ struct TcLayout {
   __host__ __device__ static constexpr size_t bytes() { return size_t(A_BYTES + B_BYTES + 128); }
 };
 
-// One pass of the predictor over CPB cells of one CTA.  Thread t < CPB*NS
-// works on cell t / NS, node t % NS; further threads of the CTA only join
-// the barriers.  `cell` is the cell index (relative to the field pointers) of
+// One pass of the predictor over the cells of one CTA (CPB of them, or fewer
+// when the launch spreads a small cell set over more CTAs).  Thread
+// t < CPB*NS works on cell t / NS, node t % NS; further threads of the CTA
+// only join the barriers.  `cell` is the cell index (relative to the field pointers) of
 // this thread's cell and `valid` whether it exists; `ihd` its 1/h_d.  Every
 // thread of the CTA must call this with the same dt, B and iters.
 template <int DIM, int N, class PDE, class Real, int TC = kTcNone, int SCHEME = 0>
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(PredictShape<DIM, N>::THREADS,
   using S = PredictShape<DIM, N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cl = threadIdx.x / S::NS;
-  const int64_t slot = int64_t(blockIdx.x) * S::CPB + cl;
+  const int64_t slot = int64_t(blockIdx.x) * (blockDim.x / S::NS) + cl;  // blockDim: cpb whole cells
   const bool valid = slot < a.count;
   const int64_t cell = valid ? int64_t(a.cells[slot]) : 0;
   double ihd[DIM];
@@ -801,8 +802,12 @@ cudaError_t launch_predict_t(const PredictArgs& a, cudaStream_t s) {
   static std::atomic<uint64_t> configured{0};
   cudaError_t e = smem_opt_in(configured, predict_kernel<DIM, N, PDE, Real, SCHEME>, smem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (a.count + S::CPB - 1) / S::CPB;
-  predict_kernel<DIM, N, PDE, Real, SCHEME><<<dim3(unsigned(blocks)), dim3(S::THREADS), smem, s>>>(a);
+  // cells per CTA: CPB, halved while the launch would have fewer than
+  // a.min_ctas CTAs (every cell's work is independent of its CTA slot)
+  int cpb = S::CPB;
+  while (a.min_ctas > 0 && cpb > 1 && (a.count + cpb - 1) / cpb < a.min_ctas) cpb = (cpb + 1) / 2;
+  const int64_t blocks = (a.count + cpb - 1) / cpb;
+  predict_kernel<DIM, N, PDE, Real, SCHEME><<<dim3(unsigned(blocks)), dim3(unsigned(cpb * S::NS)), smem, s>>>(a);
   return cudaGetLastError();
 }
 
