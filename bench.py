@@ -58,7 +58,7 @@ TF32_PEAK_TFLOPS = float(_PEAKS.get("bf16_tflops", 1900.0)) / 2
 # case of the same kernel, scaled by cells; per-cell traffic is size
 # independent).  A kernel change invalidates its entry.
 NCU_TRAFFIC_PER_CELL = {
-    "predict_kernel<3,5,Euler,double>": (173.55e6 + 457.99e6) / 19683,
+    "predict_kernel<3,5,Euler,double>": (175.51e6 + 458.56e6) / 19683,
 }
 
 WORKLOADS = {
