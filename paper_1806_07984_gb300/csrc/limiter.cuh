@@ -129,14 +129,31 @@ __device__ __forceinline__ double block_reduce(double x, bool is_max, double* re
 }
 
 // ---------------------------------------------------------------- bounds
+// Minima and maxima on the integer pipe: a double's bit pattern, with the
+// magnitude bits flipped for negative values, orders like the value (-0
+// below +0), so min/max and warp reductions need no FP64 instructions (on
+// GB300 the FP64 pipe is the scarce one).  A NaN is left out, as fmin/fmax
+// do: it maps to the neutral key of the reduction.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool is_nan_bits(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ double key_value(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
 template <int DIM, int N, class PDE>
 __global__ void __launch_bounds__(256) limiter_bounds_kernel(const LimiterArgs a) {
   using L = LimShape<DIM, N>;
   constexpr int n = L::n, S = L::S, NS = L::NS, SS = L::SS, M = PDE::M;
+  constexpr long long kNone = 0x7fffffffffffffffLL;  // neutral key of a minimum
   extern __shared__ double smem[];
   double* sA = smem;
-  double* red = sA + S * n;  // [warp][min M | max M]
-  double* U = red + 16 * M;
+  long long* red = reinterpret_cast<long long*>(sA + S * n);  // [warp][min M | max M]
+  double* U = sA + S * n + 16 * M;
   double* X = U + M * NS;
   const int64_t cell = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -148,25 +165,24 @@ __global__ void __launch_bounds__(256) limiter_bounds_kernel(const LimiterArgs a
   }
   __syncthreads();
   const double* P = subcell_partial<DIM, N, M>(U, sA, X);
-  double mn[M], mx[M];
+  long long mn[M], mx[M];  // keys; the maximum is kept negated, so both reduce by min
 #pragma unroll
-  for (int v = 0; v < M; ++v) {
-    mn[v] = INFINITY;
-    mx[v] = -INFINITY;
-  }
+  for (int v = 0; v < M; ++v) mn[v] = mx[v] = kNone;
   for (int sub = threadIdx.x; sub < SS; sub += blockDim.x)
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       const double x = sub_value<DIM, N, M>(P, sA, v, sub);
-      mn[v] = fmin(mn[v], x);
-      mx[v] = fmax(mx[v], x);
+      if (is_nan_bits(x)) continue;
+      const long long k = order_key(x);
+      mn[v] = min(mn[v], k);
+      mx[v] = min(mx[v], -k);  // -k: no overflow, k > LLONG_MIN for every non-NaN x
     }
 #pragma unroll
   for (int v = 0; v < M; ++v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      mn[v] = fmin(mn[v], __shfl_xor_sync(0xffffffffu, mn[v], o));
-      mx[v] = fmax(mx[v], __shfl_xor_sync(0xffffffffu, mx[v], o));
+      mn[v] = min(mn[v], __shfl_xor_sync(0xffffffffu, mn[v], o));
+      mx[v] = min(mx[v], __shfl_xor_sync(0xffffffffu, mx[v], o));
     }
   if (lane == 0)
 #pragma unroll
@@ -178,9 +194,10 @@ __global__ void __launch_bounds__(256) limiter_bounds_kernel(const LimiterArgs a
   if (threadIdx.x < 2 * M) {
     const int v = threadIdx.x % M;
     const bool is_max = threadIdx.x >= M;
-    double x = red[threadIdx.x];
-    for (int w = 1; w < int(blockDim.x >> 5); ++w)
-      x = is_max ? fmax(x, red[w * 2 * M + threadIdx.x]) : fmin(x, red[w * 2 * M + threadIdx.x]);
+    long long k = red[threadIdx.x];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) k = min(k, red[w * 2 * M + threadIdx.x]);
+    // all subcell values NaN: NaN, as fmin/fmax of NaNs
+    const double x = k == kNone ? __longlong_as_double(0x7ff8000000000000LL) : key_value(is_max ? -k : k);
     a.bounds[(cell * M + v) * 2 + (is_max ? 1 : 0)] = x;
   }
 }
