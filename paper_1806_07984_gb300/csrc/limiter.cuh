@@ -23,6 +23,7 @@
 // Shared-memory layouts use x fastest (subcell index sx + S sy + S^2 sz) and
 // the lowest tangential direction fastest on faces, as the face data do.
 #pragma once
+#include <climits>
 #include "faces.cuh"
 #include "kernels.h"
 #include "pde.cuh"
@@ -138,6 +139,12 @@ __device__ __forceinline__ long long order_key(double x) {
   const long long b = __double_as_longlong(x);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
+// The same key with -0 mapped to +0, for comparisons that must agree with
+// the FP64 ones (which treat the two zeros as equal).
+__device__ __forceinline__ long long compare_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b == LLONG_MIN ? 0 : (b ^ ((b >> 63) & 0x7fffffffffffffffLL));
+}
 __device__ __forceinline__ bool is_nan_bits(double x) {
   return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
 }
@@ -213,6 +220,7 @@ __global__ void __launch_bounds__(256) limiter_detect_kernel(const LimiterArgs a
   double* hi = lo + M;       // [M]
   double* U = hi + M;
   double* X = U + M * NS;
+  __shared__ long long klo[M], khi[M];
   const int64_t cell = blockIdx.x;
   load_tables<N>(a.T, sA, nullptr, nullptr);
   if (threadIdx.x < M) {
@@ -228,6 +236,10 @@ __global__ void __launch_bounds__(256) limiter_detect_kernel(const LimiterArgs a
     const double delta = fmax(a.delta0, a.eps * (h - l));
     lo[v] = l - delta;
     hi[v] = h + delta;
+    // the same bounds as order keys for the integer-pipe comparisons below;
+    // a NaN bound admits everything, as the FP64 comparisons would
+    klo[v] = is_nan_bits(lo[v]) ? LLONG_MIN : compare_key(lo[v]);
+    khi[v] = is_nan_bits(hi[v]) ? LLONG_MAX : compare_key(hi[v]);
   }
   bool bad = false;
   for (int node = threadIdx.x; node < NS; node += blockDim.x) {
@@ -252,7 +264,8 @@ __global__ void __launch_bounds__(256) limiter_detect_kernel(const LimiterArgs a
     for (int v = 0; v < M; ++v) {
       q[v] = sub_value<DIM, N, M>(P, sA, v, sub);
       fin = fin && isfinite(q[v]);
-      dmp = dmp || q[v] < lo[v] || q[v] > hi[v];
+      const long long k = compare_key(q[v]);  // a NaN value is caught by `fin`
+      dmp = dmp || k < klo[v] || k > khi[v];
     }
     bool ok = true;
     if (PDE::kPositivity) PDE::max_speed(q, 0, a.gamma, &ok);
