@@ -824,8 +824,8 @@ def time_predictor(s, torch, reps=3):
 
 def cpu_baseline(wl_name, wl, seconds=15.0, cores=1):
     """Oracle (numpy FP64, one BLAS thread per process) on a bounded sample:
-    full oracle steps on the same PDE/order/refinement rule on a base 3^3
-    mesh; with cores > 1 that many independent processes run at once and
+    full oracle steps on the same PDE, order, bubble and refinement rule (ball
+    radius) on a base 3^3 mesh; with cores > 1 that many independent processes run at once and
     their throughputs add up."""
     code = r"""
 import os, sys, time, json
@@ -839,9 +839,9 @@ B = basis.Basis(order)
 c = workloads.sphere_center(0.0)[:dim]
 u = np.zeros((len(m.cells), 1) + (2,) * dim)
 for _ in range(lvl):
-    u = m.remesh(u, omesh.sphere_flags(m, c, max(radius, 0.2)), basis.Basis(1))
+    u = m.remesh(u, omesh.sphere_flags(m, c, radius), basis.Basis(1))
 X = m.node_coords(B.xi)
-u = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X, sigma=0.15), 0, 1))
+u = np.ascontiguousarray(np.moveaxis(workloads.density_bubble(X), 0, 1))
 P = opde.Euler(dim)
 h = m.cell_widths()
 dt = ader.cfl_dt(u, h, P, order, cfl=workloads.ADER_CFL[order])
@@ -874,8 +874,9 @@ print(json.dumps(dict(value=dofs * steps / el, cells=len(m.cells), steps=steps, 
             return {"error": err[-400:]}
         results.append(json.loads(out.strip().splitlines()[-1]))
     res = results[0]
-    what = (f"{res['steps']} oracle steps of the same PDE/order/AMR rule on a base-3^{wl['dim']} mesh "
-            f"with {res['cells']} cells ({res['seconds']:.1f} s, numpy FP64, 1 BLAS thread)")
+    what = (f"{res['steps']} oracle steps of the same PDE, order, bubble and refinement ball on a "
+            f"base-3^{wl['dim']} mesh with {res['cells']} cells ({res['seconds']:.1f} s, numpy FP64, "
+            f"1 BLAS thread)")
     if cores > 1:
         what = f"{cores} concurrent processes, each " + what
     return {"value": sum(r["value"] for r in results), "unit": "DoF-updates/s", "cores": cores,
