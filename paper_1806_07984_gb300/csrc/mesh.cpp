@@ -257,13 +257,31 @@ bool Tree::build() {
 
 void Tree::classify(const int8_t* refine_flags) {
   const size_t n = cells.size();
+  // The split in contiguous cell ranges: per-range skeleton counts, then each
+  // range fills both lists from its own offsets (the lists stay ascending).
   skeleton.assign(n, 0);
-  skel_cells.clear();
-  encl_cells.clear();
-  for (size_t i = 0; i < n; ++i) {
-    skeleton[i] = transition[i] || (refine_flags && refine_flags[i] > 0);
-    (skeleton[i] ? skel_cells : encl_cells).push_back(int32_t(i));
-  }
+  const int Tc = pass_threads(int64_t(n));
+  std::vector<int64_t> nsk(size_t(Tc) + 1, 0);
+  parallel_ranges(int64_t(n), Tc, [&](int t, int64_t b, int64_t e) {
+    int64_t c = 0;
+    for (int64_t i = b; i < e; ++i) {
+      skeleton[size_t(i)] = transition[size_t(i)] || (refine_flags && refine_flags[i] > 0);
+      c += skeleton[size_t(i)];
+    }
+    nsk[size_t(t) + 1] = c;
+  });
+  for (int t = 0; t < Tc; ++t) nsk[size_t(t) + 1] += nsk[size_t(t)];
+  skel_cells.resize(size_t(nsk[size_t(Tc)]));
+  encl_cells.resize(n - size_t(nsk[size_t(Tc)]));
+  parallel_ranges(int64_t(n), Tc, [&](int t, int64_t b, int64_t e) {
+    int64_t ps = nsk[size_t(t)], pe = b - nsk[size_t(t)];
+    for (int64_t i = b; i < e; ++i) {
+      if (skeleton[size_t(i)])
+        skel_cells[size_t(ps++)] = int32_t(i);
+      else
+        encl_cells[size_t(pe++)] = int32_t(i);
+    }
+  });
   // enclave pipeline: chunk of every cell (-1 = skeleton), faces by the later
   // chunk of their two cells, cells by the latest chunk among their faces.
   // conf = the faces with two skeleton cells (conf_all order), then the
@@ -323,12 +341,28 @@ void Tree::classify(const int8_t* refine_flags) {
     std::vector<int64_t>& at = cnt[size_t(t)];
     for (int64_t f = b; f < e; ++f) conf[size_t(at[size_t(group[size_t(f)] + 1)]++)] = conf_all[size_t(f)];
   });
+  // corrector groups: the same two-pass scheme over cell ranges
+  std::vector<std::vector<int64_t>> gc(size_t(Tc), std::vector<int64_t>(size_t(K) + 1, 0));
+  parallel_ranges(int64_t(n), Tc, [&](int t, int64_t b, int64_t e) {
+    std::vector<int64_t>& C = gc[size_t(t)];
+    for (int64_t i = b; i < e; ++i) ++C[size_t(ready[size_t(i)] + 1)];
+  });
   corr_off.assign(size_t(K) + 2, 0);
-  for (size_t i = 0; i < n; ++i) ++corr_off[size_t(ready[i] + 1) + 1];
+  for (int t = 0; t < Tc; ++t)
+    for (int g = 0; g <= K; ++g) corr_off[size_t(g) + 1] += gc[size_t(t)][size_t(g)];
   for (int g = 0; g <= K; ++g) corr_off[size_t(g) + 1] += corr_off[size_t(g)];
+  std::vector<int64_t> at(corr_off.begin(), corr_off.end() - 1);
+  for (int t = 0; t < Tc; ++t)  // gc[t] becomes range t's first slot in each group
+    for (int g = 0; g <= K; ++g) {
+      const int64_t c = gc[size_t(t)][size_t(g)];
+      gc[size_t(t)][size_t(g)] = at[size_t(g)];
+      at[size_t(g)] += c;
+    }
   corr_cells.assign(n, 0);
-  std::vector<int64_t> fill(corr_off.begin(), corr_off.end() - 1);
-  for (size_t i = 0; i < n; ++i) corr_cells[size_t(fill[size_t(ready[i] + 1)]++)] = int32_t(i);
+  parallel_ranges(int64_t(n), Tc, [&](int t, int64_t b, int64_t e) {
+    std::vector<int64_t>& A = gc[size_t(t)];
+    for (int64_t i = b; i < e; ++i) corr_cells[size_t(A[size_t(ready[size_t(i)] + 1)]++)] = int32_t(i);
+  });
 }
 
 void Tree::refine_around(const uint8_t* troubled, int8_t* flags) const {
