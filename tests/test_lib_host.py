@@ -184,13 +184,14 @@ def test_refine_around_matches_oracle(A, dim, base, centers):
         A.ader_mesh_destroy(lm)
 
 
-@pytest.mark.parametrize("K", [1, 3, 8])
-def test_pipeline_lists(A, K):
+@pytest.mark.parametrize("K,base,levels", [(1, 3, 2), (3, 3, 2), (8, 3, 2), (8, 20, 1)])
+def test_pipeline_lists(A, K, base, levels):
     """Enclave pipeline lists: chunks partition the enclave, every conforming
     face sits after the skeleton faces in the stage of the later chunk of its
     two cells, and every cell is corrected exactly once, in the stage after
-    which all its faces are solved."""
-    om, lm, keys = _pair(A, 3, 3, 2, [(0.5, 0.5, 0.5), (0.5, 0.5, 0.5)], 0.2)
+    which all its faces are solved.  The base-20 mesh (> 8,192 cells) takes the
+    multi-threaded passes of the classification."""
+    om, lm, keys = _pair(A, 3, base, levels, [(0.5, 0.5, 0.5)] * levels, 0.2)
     try:
         C = len(keys)
         _, skel = A.ader_mesh_leaves(lm)
