@@ -455,23 +455,29 @@ bool Tree::remesh(const int8_t* flags, std::vector<TransferItem>* plan,
   });
   std::sort(fams.begin(), fams.end());
   fams.erase(std::unique(fams.begin(), fams.end()), fams.end());
-  std::vector<Key> approved;
+  // the checks only read the sets: families in parallel ranges, applied in order
+  std::vector<uint8_t> ok_fam(fams.size(), 0);
   const int nz = dim_ == 3 ? 3 : 1;
-  for (uint64_t v : fams) {
-    Key P = unpack(v);
-    bool ok = true;
-    for (int sz = 0; sz < nz && ok; ++sz)
-      for (int sy = 0; sy < 3 && ok; ++sy)
-        for (int sx = 0; sx < 3 && ok; ++sx) {
-          int s[3] = {sx, sy, sz};
-          const uint64_t c = pack(child(P, s));
-          if (!leaves_.count(c) || !coarsen.count(c)) ok = false;
-        }
-    for (int dir = 0; dir < dim_ && ok; ++dir)
-      for (int side = 0; side < 2 && ok; ++side)
-        if (max_level_across(P, dir, side) >= P.level + 2) ok = false;
-    if (ok) approved.push_back(P);
-  }
+  parallel_ranges(int64_t(fams.size()), pass_threads(int64_t(fams.size()) * 32), [&](int, int64_t b, int64_t e) {
+    for (int64_t f = b; f < e; ++f) {
+      const Key P = unpack(fams[size_t(f)]);
+      bool ok = true;
+      for (int sz = 0; sz < nz && ok; ++sz)
+        for (int sy = 0; sy < 3 && ok; ++sy)
+          for (int sx = 0; sx < 3 && ok; ++sx) {
+            int s[3] = {sx, sy, sz};
+            const uint64_t c = pack(child(P, s));
+            if (!leaves_.count(c) || !coarsen.count(c)) ok = false;
+          }
+      for (int dir = 0; dir < dim_ && ok; ++dir)
+        for (int side = 0; side < 2 && ok; ++side)
+          if (max_level_across(P, dir, side) >= P.level + 2) ok = false;
+      ok_fam[size_t(f)] = ok ? 1 : 0;
+    }
+  });
+  std::vector<Key> approved;
+  for (size_t f = 0; f < fams.size(); ++f)
+    if (ok_fam[f]) approved.push_back(unpack(fams[f]));
   for (const Key& P : approved) {
     for (int sz = 0; sz < nz; ++sz)
       for (int sy = 0; sy < 3; ++sy)
